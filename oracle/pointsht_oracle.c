@@ -1,0 +1,266 @@
+/*
+ * pointsht_oracle.c -- plain FP64 CPU oracle for the direct, pixel-free
+ * spherical-harmonic transform of a weighted point catalog.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or constant with the
+ * CUDA library.
+ *
+ * What it computes, in the paper's own order and notation
+ * (Baleato Lizancos & White, "Harmonic analysis of discrete tracers of
+ * large-scale structure", arXiv:2312.12285):
+ *
+ *   a_lm = sum_i w_i Y*_lm(theta_i, phi_i)                       (Eq. alm_def)
+ *   Y_lm = sqrt((2l+1)/4pi) Pbar_l^m(x) e^{i m phi},  x = cos(theta),
+ *          m >= 0                                                  (App. A)
+ *   Pbar_0^0 = 1
+ *   Pbar_m^m = -sqrt(1-x^2) sqrt(1 - 1/(2m)) Pbar_{m-1}^{m-1}      (App. A)
+ *   Pbar_{m+1}^m = sqrt(2m+1) x Pbar_m^m                            (App. A)
+ *   Pbar_l^m = sqrt((l-m)/(l+m)) [ (2l-1)/(l-m) x Pbar_{l-1}^m
+ *              - sqrt((l-m-1)/(l+m-1)) (l+m-1)/(l-m) Pbar_{l-2}^m ] (App. A)
+ *
+ * The paper is silent on underflow: Pbar_m^m ~ (1-x^2)^{m/2} leaves the
+ * FP64 range for large m near the poles.  Every Pbar here is therefore
+ * carried as a mantissa with a separate binary exponent (value = v * 2^e),
+ * rescaled by exact powers of two only, and converted to a double with
+ * ldexp() at the point of use, so that each value is the correctly rounded
+ * FP64 number of the scaled recurrence (tiny values round to 0 or to a
+ * subnormal, exactly as plain FP64 would give them, nothing is cut off).
+ *
+ * Summation over points uses Neumaier-compensated FP64 sums over a fixed
+ * partition of the point range (64 contiguous ranges, combined in order), so
+ * results are independent of the number of threads.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_PI 3.14159265358979323846264338327950288
+#define ORACLE_NBLOCKS 64
+/* rescaling unit of the mantissa/exponent representation */
+#define ORACLE_SCALE_BITS 256
+
+/* Neumaier compensated accumulator. */
+typedef struct { double s, c; } nsum;
+
+static inline void nsum_add(nsum* a, double v) {
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else a->c += (v - t) + a->s;
+    a->s = t;
+}
+static inline double nsum_val(const nsum* a) { return a->s + a->c; }
+
+/* Recurrence coefficients of App. A for one order m, l = m+2..lmax:
+ *   c1[l] = sqrt((l-m)/(l+m)) (2l-1)/(l-m)
+ *   c2[l] = sqrt((l-m)/(l+m)) sqrt((l-m-1)/(l+m-1)) (l+m-1)/(l-m)
+ * so that Pbar_l = c1[l] x Pbar_{l-1} - c2[l] Pbar_{l-2}.                  */
+static void pbar_coeffs(int lmax, int m, double* c1, double* c2) {
+    for (int l = m + 2; l <= lmax; ++l) {
+        double lm = (double)(l - m), lp = (double)(l + m);
+        double r = sqrt(lm / lp);
+        c1[l] = r * (2.0 * l - 1.0) / lm;
+        c2[l] = r * sqrt((lm - 1.0) / (lp - 1.0)) * (lp - 1.0) / lm;
+    }
+}
+
+/* Sectoral value Pbar_m^m(x) as (v, e), value = v * 2^e, by the App. A
+ * recurrence taken from Pbar_0^0 = 1 upward in m.                          */
+static void pbar_sectoral(double x, int m, double* v_out, int* e_out) {
+    double s = sqrt((1.0 - x) * (1.0 + x)); /* sqrt(1-x^2) */
+    double v = 1.0;
+    int e = 0;
+    for (int k = 1; k <= m; ++k) {
+        v *= -s * sqrt(1.0 - 1.0 / (2.0 * k));
+        if (v != 0.0 && fabs(v) < 0x1p-256) {
+            v *= 0x1p256;
+            e -= ORACLE_SCALE_BITS;
+        }
+    }
+    *v_out = v;
+    *e_out = e;
+}
+
+/* Pbar_l^m(x) for l = m..lmax (App. A), written as mantissa/exponent pairs
+ * (value = mant[l-m] * 2^expo[l-m]).  c1/c2 are from pbar_coeffs().        */
+static void pbar_column_scaled(double x, int lmax, int m, const double* c1,
+                               const double* c2, double* mant, int* expo) {
+    double v0;
+    int e;
+    pbar_sectoral(x, m, &v0, &e);
+    mant[0] = v0;
+    expo[0] = e;
+    if (lmax == m) return;
+    double v1 = sqrt(2.0 * m + 1.0) * x * v0; /* Pbar_{m+1}^m */
+    mant[1] = v1;
+    expo[1] = e;
+    double pm2 = v0, pm1 = v1;
+    for (int l = m + 2; l <= lmax; ++l) {
+        double p = c1[l] * x * pm1 - c2[l] * pm2;
+        pm2 = pm1;
+        pm1 = p;
+        if (e < 0 && fabs(p) > 0x1p256) {
+            /* both carried values share the exponent: rescale both exactly */
+            pm1 *= 0x1p-256;
+            pm2 *= 0x1p-256;
+            e += ORACLE_SCALE_BITS;
+        }
+        mant[l - m] = pm1;
+        expo[l - m] = e;
+    }
+}
+
+/* ---------------------------------------------------------------- API --- */
+
+/* Pbar_l^m(x), l = m..lmax, as mantissa/exponent pairs (for pins that need
+ * values below the FP64 range).                                            */
+void oracle_pbar_scaled(double x, int lmax, int m, double* mant, int* expo) {
+    double* c1 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+    double* c2 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+    pbar_coeffs(lmax, m, c1, c2);
+    pbar_column_scaled(x, lmax, m, c1, c2, mant, expo);
+    free(c1);
+    free(c2);
+}
+
+/* Y_lm(theta, phi) for l = m..lmax at one point (App. A + Eq. for Y_lm),
+ * out interleaved (re, im), length 2*(lmax-m+1).                          */
+void oracle_ylm(double x, double phi, int lmax, int m, double* out) {
+    int len = lmax - m + 1;
+    double* mant = (double*)malloc(sizeof(double) * (size_t)len);
+    int* expo = (int*)malloc(sizeof(int) * (size_t)len);
+    oracle_pbar_scaled(x, lmax, m, mant, expo);
+    double c = cos((double)m * phi), s = sin((double)m * phi);
+    for (int l = m; l <= lmax; ++l) {
+        double lam = sqrt((2.0 * l + 1.0) / (4.0 * ORACLE_PI)) *
+                     ldexp(mant[l - m], expo[l - m]);
+        out[2 * (l - m)] = lam * c;
+        out[2 * (l - m) + 1] = lam * s;
+    }
+    free(mant);
+    free(expo);
+}
+
+/* a_lm = sum_i w_i Y*_lm(n_i)  (Eq. alm_def) for the orders listed in mlist.
+ * Output: for each listed m (in list order) the column l = m..lmax,
+ * interleaved (re, im), packed one column after another.  Returns 0 on
+ * success, -1 on a bad argument, -2 on allocation failure.                */
+int oracle_alm(int64_t n, const double* x, const double* phi, const double* w,
+               int lmax, int nm, const int* mlist, double* out, int nthreads) {
+    if (n < 0 || lmax < 0 || nm < 0) return -1;
+    for (int k = 0; k < nm; ++k)
+        if (mlist[k] < 0 || mlist[k] > lmax) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int64_t off = 0;
+    int status = 0;
+    for (int k = 0; k < nm; ++k) {
+        const int m = mlist[k];
+        const int len = lmax - m + 1;
+        double* c1 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* c2 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* norm = (double*)malloc(sizeof(double) * (size_t)len);
+        nsum* blk = (nsum*)calloc((size_t)ORACLE_NBLOCKS * 2 * (size_t)len, sizeof(nsum));
+        if (!c1 || !c2 || !norm || !blk) {
+            free(c1); free(c2); free(norm); free(blk);
+            return -2;
+        }
+        pbar_coeffs(lmax, m, c1, c2);
+        for (int l = m; l <= lmax; ++l)
+            norm[l - m] = sqrt((2.0 * l + 1.0) / (4.0 * ORACLE_PI));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int b = 0; b < ORACLE_NBLOCKS; ++b) {
+            int64_t i0 = n * b / ORACLE_NBLOCKS, i1 = n * (b + 1) / ORACLE_NBLOCKS;
+            double* mant = (double*)malloc(sizeof(double) * (size_t)len);
+            int* expo = (int*)malloc(sizeof(int) * (size_t)len);
+            nsum* acc = blk + (size_t)b * 2 * (size_t)len;
+            if (!mant || !expo) {
+#pragma omp critical
+                status = -2;
+                free(mant); free(expo);
+                continue;
+            }
+            for (int64_t i = i0; i < i1; ++i) {
+                pbar_column_scaled(x[i], lmax, m, c1, c2, mant, expo);
+                /* w Y* = w lambda (cos m phi - i sin m phi) */
+                double ph = (double)m * phi[i];
+                double wc = w[i] * cos(ph), ws = -w[i] * sin(ph);
+                for (int q = 0; q < len; ++q) {
+                    double lam = norm[q] * ldexp(mant[q], expo[q]);
+                    nsum_add(&acc[2 * q], lam * wc);
+                    nsum_add(&acc[2 * q + 1], lam * ws);
+                }
+            }
+            free(mant);
+            free(expo);
+        }
+        for (int q = 0; q < len; ++q) {
+            nsum re = {0.0, 0.0}, im = {0.0, 0.0};
+            for (int b = 0; b < ORACLE_NBLOCKS; ++b) {
+                nsum_add(&re, nsum_val(&blk[(size_t)b * 2 * len + 2 * q]));
+                nsum_add(&im, nsum_val(&blk[(size_t)b * 2 * len + 2 * q + 1]));
+            }
+            out[2 * (off + q)] = nsum_val(&re);
+            out[2 * (off + q) + 1] = nsum_val(&im);
+        }
+        off += len;
+        free(c1); free(c2); free(norm); free(blk);
+        if (status) return status;
+    }
+    return status;
+}
+
+/* Point-evaluation of sum_{l,m>=0} lambda_lm(x_i) Re(g_lm e^{i m phi_i}) for
+ * listed points: the adjoint of oracle_alm with respect to w_i, written from
+ * the same definition (d a_lm / d w_i = Y*_lm(n_i)).  g is the full packed
+ * m-major triangle (index m(2L+1-m)/2 + l), interleaved (re, im).          */
+int oracle_adjoint(int64_t n, const double* x, const double* phi, int lmax,
+                   const double* g, double* out, int nthreads) {
+    if (n < 0 || lmax < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int status = 0;
+#pragma omp parallel
+    {
+        double* c1 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* c2 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* mant = (double*)malloc(sizeof(double) * ((size_t)lmax + 1));
+        int* expo = (int*)malloc(sizeof(int) * ((size_t)lmax + 1));
+        if (!c1 || !c2 || !mant || !expo) {
+#pragma omp critical
+            status = -2;
+        } else {
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t i = 0; i < n; ++i) {
+                nsum acc = {0.0, 0.0};
+                for (int m = 0; m <= lmax; ++m) {
+                    pbar_coeffs(lmax, m, c1, c2);
+                    pbar_column_scaled(x[i], lmax, m, c1, c2, mant, expo);
+                    double ph = (double)m * phi[i];
+                    double c = cos(ph), s = sin(ph);
+                    int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+                    for (int l = m; l <= lmax; ++l) {
+                        double lam = sqrt((2.0 * l + 1.0) / (4.0 * ORACLE_PI)) *
+                                     ldexp(mant[l - m], expo[l - m]);
+                        const double* gl = g + 2 * (base + l);
+                        nsum_add(&acc, lam * (gl[0] * c - gl[1] * s));
+                    }
+                }
+                out[i] = nsum_val(&acc);
+            }
+        }
+        free(c1); free(c2); free(mant); free(expo);
+    }
+    return status;
+}
