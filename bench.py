@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Throughput of the direct point-catalog SHT on GB300 (arXiv:2312.12285).
+
+One step = one pass of the whole forward hot path over the workload:
+point preparation, per-(point, m) seed and phase, l-recurrence and
+accumulation into a_lm (analysis kernel), reduction over chunks, shot noise,
+pseudo-C_l and 32 log-spaced bandpowers.  The metric is nominal
+points x modes per second (modes = (lmax+1)(lmax+2)/2 per point).
+
+Default workload: 1e6 lognormal galaxies + 9e6 randoms in a 40%-sky cap mask,
+lmax = 2048, FP32 recurrence with FP64-accurate seed and phase.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every catalog is split into N
+contiguous shards, each rank transforms its shard and the partial a_lm are
+summed with one NCCL all-reduce (the sum over points is the only exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "a_lm points*modes/s at lmax=2048, mixed vs FP64 at C_l err 1e-4; roofline %"
+UNIT = "points*modes/s"
+FLOPS_PER_POINT_MODE = 7  # recurrence: 1 mul + 1 FMA; accumulation: 2 FMA (Sec. 2.2 / App. A)
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=3, help="workload configuration (3 = lmax 2048, 1e7 points)")
+    ap.add_argument("--scale", type=float, default=1.0, help="scale the point counts (profiling runs)")
+    ap.add_argument("--lmax", type=int, default=None)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------- helpers --
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("analysis.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2312_12285_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, npoints: int):
+    """DRAM bytes per launch of the analysis kernel from a committed ncu summary,
+    scaled to this launch's points; None if absent or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "analysis_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    per_pt = d.get("dram_bytes_per_launch") / max(1, d.get("points"))
+    return per_pt * npoints
+
+
+def shard(arr, rank, world):
+    n = arr.shape[0]
+    return arr[n * rank // world: n * (rank + 1) // world]
+
+
+def load_workload(args):
+    from paper_2312_12285_gb300 import catalogs
+    wl = catalogs.config(args.config, scale=args.scale, lmax=args.lmax)
+    if args.precision == "fp64":
+        for c in wl.catalogs:
+            c.x, c.phi, c.w = (v.astype("float64") for v in (c.x, c.phi, c.w))
+    return wl
+
+
+def workload_name(wl, args) -> str:
+    parts = [f"{c.name} {c.n:.3g}" for c in wl.catalogs]
+    return f"{wl.name}: " + " + ".join(parts) + f", lmax {wl.lmax}, {args.precision}"
+
+
+def oracle_sample(wl, target_pm: float):
+    """A bounded sample of the workload: the first points of every catalog in
+    proportion to its size, about target_pm points*modes in total."""
+    nm = wl.nmodes
+    ntot = wl.npoints
+    npts = max(len(wl.catalogs), int(target_pm / nm))
+    frac = min(1.0, npts / ntot)
+    out = []
+    for c in wl.catalogs:
+        k = max(1, int(round(c.n * frac)))
+        out.append((c.x[:k], c.phi[:k], c.w[:k], c.coeff, c.field))
+    return out
+
+
+def run_oracle(sample, lmax, nfield=1):
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    alms = []
+    for f in range(nfield):
+        sel = [(x, p, w, co) for (x, p, w, co, fi) in sample if fi == f]
+        alms.append(oracle.field_alm(sel, lmax) if sel else np.zeros(oracle.nmodes(lmax), np.complex128))
+    dt = time.perf_counter() - t0
+    return alms, dt
+
+
+# --------------------------------------------------------------- reference --
+def reference_arm(args):
+    """The FP64 CPU oracle timed on this machine's host cores, each step a
+    bounded sample of the same workload (the paper's method written plainly)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = load_workload(args)
+    L = wl.lmax
+    target = 3.0e9 if L >= 1024 else 5.0e8
+    sample = oracle_sample(wl, target)
+    npts = sum(s[0].shape[0] for s in sample)
+    pm = npts * wl.nmodes
+    for _ in range(args.warmup):
+        run_oracle(sample, L, wl.nfield)
+    times = []
+    for _ in range(args.steps):
+        _, dt = run_oracle(sample, L, wl.nfield)
+        times.append(dt)
+    t = sum(times) / len(times)
+    val = pm / t
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(wl, args), "points": wl.npoints, "lmax": L, "nmodes": wl.nmodes},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {npts} points of the workload (proportional per catalog), "
+                                   f"all {wl.nmodes} modes, FP64 C oracle, OpenMP"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours --
+def ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2312_12285_gb300 import catalogs, ops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = load_workload(args)
+    L = wl.lmax
+    prec = args.precision
+    # this rank's shard of every catalog
+    cats_np = [(shard(c.x, rank, world), shard(c.phi, rank, world), shard(c.w, rank, world), c.field, c.coeff)
+               for c in wl.catalogs]
+    n_rank = sum(c[0].shape[0] for c in cats_np)
+    cats = [ops.Cat(torch.from_numpy(np.ascontiguousarray(x)).to(dev), torch.from_numpy(np.ascontiguousarray(p)).to(dev),
+                    torch.from_numpy(np.ascontiguousarray(w)).to(dev), f, co) for (x, p, w, f, co) in cats_np]
+    nfield = wl.nfield
+    plan = ops.get_plan(L, dev)
+    ws = torch.empty(ops.workspace_bytes(plan, cats, nfield, prec), dtype=torch.uint8, device=dev)
+    out = torch.empty((nfield, plan.nmodes), dtype=torch.complex128, device=dev)
+    edges = torch.from_numpy(catalogs.log_bin_edges(L, 32).astype(np.int32)).to(dev)
+
+    def step(cs=cats):
+        a = ops.alm_raw(plan, cs, nfield, prec, out=out, workspace=ws)
+        noise = ops.shot_noise_raw(cs, nfield, prec, dev, workspace=ws)
+        if dist is not None:
+            dist.all_reduce(torch.view_as_real(a))
+            dist.all_reduce(noise)
+        cl = ops.cl_raw(a, noise)
+        cb = ops.bin_raw(cl, edges)
+        return cl, cb
+
+    launches_per_step = 7  # prep, analysis, reduce, 2 x shot noise, C_l, bins
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+
+    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in evk:  # create the event handles before they are handed to the library
+        a_.record()
+        b_.record()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record()
+    for k in range(args.steps):
+        plan.set_timing_events(evk[k][0], evk[k][1])
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    plan.set_timing_events(None, None)
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    kms = sum(a.elapsed_time(b) for a, b in evk) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms, kms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kms = float(t[0]), float(t[1])
+    plan.check()
+
+    total_pm = wl.npoints * wl.nmodes
+    value = total_pm / (ms / 1e3)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = None
+    try:
+        sm_max = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz")
+    except Exception:
+        pass
+    sm_max = sm_max or 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s FP32
+    achieved = FLOPS_PER_POINT_MODE * n_rank * wl.nmodes / (kms / 1e3) / 1e12
+    traffic = profiled_traffic(wl.name, n_rank)
+
+    # ---- end to end through the public API, host buffers in pinned memory ----
+    e2e = None
+    if not args.no_e2e:
+        host = [(torch.from_numpy(np.ascontiguousarray(x)).pin_memory(), torch.from_numpy(np.ascontiguousarray(p)).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(w)).pin_memory()) for (x, p, w, f, co) in cats_np]
+        dcats = [ops.Cat(torch.empty_like(h[0], device=dev), torch.empty_like(h[1], device=dev),
+                         torch.empty_like(h[2], device=dev), c.field, c.coeff) for h, c in zip(host, cats)]
+        cl_h = torch.empty((nfield * (nfield + 1) // 2, L + 1), dtype=torch.float64).pin_memory()
+        cb_h = torch.empty((nfield * (nfield + 1) // 2, 32), dtype=torch.float64).pin_memory()
+        h2d = sum(sum(t.numel() * t.element_size() for t in h) for h in host)
+        d2h = cl_h.numel() * 8 + cb_h.numel() * 8
+
+        def e2e_step():
+            for h, d in zip(host, dcats):
+                d.x.copy_(h[0], non_blocking=True)
+                d.phi.copy_(h[1], non_blocking=True)
+                d.w.copy_(h[2], non_blocking=True)
+            cl, cb = step(dcats)
+            cl_h.copy_(cl, non_blocking=True)
+            cb_h.copy_(cb, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        s1.record()
+        torch.cuda.synchronize()
+        ems = s0.elapsed_time(s1) / args.steps
+        if dist is not None:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t[0])
+        e2e = {"value": total_pm / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ems}
+
+    # ---- CPU oracle baseline and accuracy on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        target = args.cpu_sample * wl.nmodes if args.cpu_sample else (1.2e10 if L >= 1024 else 1e9)
+        sample = oracle_sample(wl, target)
+        npts = sum(s[0].shape[0] for s in sample)
+        ref, dt = run_oracle(sample, L, nfield)
+        cpu = {"value": npts * wl.nmodes / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {npts} points of the workload (proportional per catalog), all {wl.nmodes} "
+                         f"modes, {dt:.1f} s"}
+        import oracle
+        scats = [ops.Cat(torch.from_numpy(np.ascontiguousarray(x)).to(dev), torch.from_numpy(np.ascontiguousarray(p)).to(dev),
+                         torch.from_numpy(np.ascontiguousarray(w)).to(dev), f, co) for (x, p, w, co, f) in sample]
+        a = ops.alm_raw(plan, scats, nfield, prec).cpu().numpy()
+        errs = []
+        for f in range(nfield):
+            tot = oracle.cl(ref[f], ref[f], L)
+            errs.append(float(np.max(np.abs(oracle.cl(a[f], a[f], L)[1:] - tot[1:]) / tot[1:])))
+        accuracy = {"cl_err_vs_fp64_oracle": max(errs), "alm_rel_err_per_l": max(
+            oracle.rel_err_per_l(a[f], ref[f], L) for f in range(nfield)),
+            "sample_points": npts, "definition": "max over 1<=l<=lmax of |C_l - C_l^ref| / C_l^ref"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(wl, args), "points": wl.npoints, "lmax": L, "nmodes": wl.nmodes,
+                       "fields": nfield, "l2": "inputs larger than L2 (prepared points 24 B x 1e7 = 240 MB)",
+                       "parallelism": f"points sharded over {world} GPU(s), one all-reduce of a_lm"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "analysis_kernel<TraitsF32,8,4>", "kernel_ms": kms,
+                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                                        f"{sm_max:.0f} MHz (recipe unit counts and clock)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "accuracy": accuracy,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * pointsht.h -- C ABI of libpointsht: the direct, pixel-free spherical-harmonic
+ * transform of weighted point catalogs, its pseudo-C_l and its adjoint, on one
+ * GB300 GPU (sm_103a).
+ *
+ * Method: Baleato Lizancos & White, "Harmonic analysis of discrete tracers of
+ * large-scale structure", arXiv:2312.12285.
+ *   a_lm = sum_i w_i Y*_lm(theta_i, phi_i)                      (Eq. alm_def)
+ *   field = data - alpha * randoms, transformed as one signed-weight sum
+ *                                                          (Sec. 2.1, Sec. 2.3)
+ *   C_l  = 1/(2l+1) sum_{m=-l..l} |a_lm|^2                      (Eq. pseudoCl)
+ *   Y_lm = sqrt((2l+1)/4pi) Pbar_l^m(cos theta) e^{i m phi}     (App. A)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller unless a
+ *   comment says "host".  The library never frees caller memory.  Apart from
+ *   pointsht_plan_create (which allocates the plan's coefficient tables) no
+ *   call allocates device memory: scratch space is the caller's workspace.
+ * - Every call is asynchronous on the caller's CUDA stream `stream`
+ *   (a cudaStream_t passed as void*; NULL = legacy default stream) and
+ *   returns after enqueueing.  Argument errors are detected on the host and
+ *   returned synchronously before anything is enqueued.  Errors found by a
+ *   kernel (an input outside its domain, a bounded wait that gave up) are
+ *   recorded in the plan and returned by pointsht_plan_check().
+ * - Coefficients for m >= 0 only are stored (a_{l,-m} = (-1)^m conj(a_lm) for
+ *   real weights, Sec. 2.2).  A set of coefficients for 0 <= m <= l <= lmax is
+ *   a packed m-major triangle of M = (lmax+1)(lmax+2)/2 complex128 values
+ *   (interleaved re, im), index(l, m) = m*(2*lmax+1-m)/2 + l.  The
+ *   Condon-Shortley phase is included (the minus sign of the sectoral
+ *   recurrence, App. A).
+ * - Outputs are overwritten, never accumulated into.  Results are bitwise
+ *   reproducible run to run for the same inputs and tuning (fixed reduction
+ *   order, no floating-point atomics).
+ * - Point coordinates: x = cos(theta) in [-1, 1], phi in radians (any finite
+ *   value; reduced modulo 2pi internally).  Dtype follows the precision:
+ *   double for POINTSHT_FP64, float for POINTSHT_FP32 / POINTSHT_MIXED.
+ * - pointsht_last_error() returns a thread-local message for the last
+ *   non-OK status returned on the calling thread.
+ */
+#ifndef POINTSHT_H
+#define POINTSHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    POINTSHT_OK = 0,
+    POINTSHT_EINVAL = 1,   /* bad argument: null pointer, size, lmax, field index, alignment */
+    POINTSHT_ERANGE = 2,   /* an input value outside its domain (|x| > 1, non-finite) */
+    POINTSHT_ENOMEM = 3,   /* workspace too small, or plan allocation failed */
+    POINTSHT_ECUDA = 4,    /* a CUDA runtime call failed (message has the CUDA error) */
+    POINTSHT_EARCH = 5,    /* current device is not a compute-capability 10.3 GPU */
+    POINTSHT_ETIMEOUT = 6  /* a bounded wait inside a kernel gave up */
+} pointsht_status;
+
+typedef enum {
+    POINTSHT_FP64 = 0,  /* FP64 recurrence (App. A) on double inputs */
+    POINTSHT_FP32 = 1,  /* FP32 recurrence, FP64-accurate seed and phase, FP64 sums */
+    POINTSHT_MIXED = 2  /* FP32 recurrence, per-m contraction on tensor cores (fp16 hi+lo) */
+} pointsht_precision;
+
+/* One point catalog contributing to one output field with a coefficient:
+ * +1 for data, -alpha for randoms (field n_g - alpha n_r, Sec. 2.1).  The
+ * catalogs of one field are transformed together as one signed-weight sum.
+ * Catalogs of one field must be different point sets. */
+typedef struct {
+    const void* x;    /* device, n values of cos(theta) */
+    const void* phi;  /* device, n azimuths (radians) */
+    const void* w;    /* device, n weights */
+    int64_t n;        /* number of points, >= 0 */
+    int32_t field;    /* output field index, 0 <= field < nfield */
+    int32_t pad_;     /* set to 0 */
+    double coeff;     /* coefficient of this catalog in its field */
+} pointsht_catalog;
+
+/* Opaque plan: recurrence tables for one lmax on one device.  Creating it
+ * allocates and fills device tables (this is the only allocating call). */
+typedef struct pointsht_plan_s* pointsht_plan;
+
+/* Library version string, e.g. "1.0.0". */
+const char* pointsht_version(void);
+
+/* Message for the last non-OK status returned on this thread. */
+const char* pointsht_last_error(void);
+
+/* Create a plan for multipoles 0..lmax (1 <= lmax <= 8192) on the current CUDA
+ * device.  Builds, in FP64 on the host, the recurrence tables of the
+ * normalised functions lambda_lm = sqrt((2l+1)/4pi) Pbar_l^m (App. A) and
+ * copies them to the device.  Returns EARCH on a device that is not sm_103,
+ * ENOMEM if an allocation fails.  *out receives the plan (host handle). */
+pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out);
+
+/* Release a plan (synchronises its device).  NULL is ignored. */
+void pointsht_plan_destroy(pointsht_plan plan);
+
+/* lmax of a plan, or -1 for NULL. */
+int32_t pointsht_plan_lmax(pointsht_plan plan);
+
+/* Wait for the plan's device, then read and clear the error flags that
+ * kernels recorded since the last check: returns ERANGE if some x was outside
+ * [-1, 1] or some input was non-finite, ETIMEOUT if a bounded wait gave up,
+ * OK otherwise. */
+pointsht_status pointsht_plan_check(pointsht_plan plan);
+
+/* Timing hook: while set, every pointsht_alm call on this plan records
+ * `start` on its stream immediately before launching the analysis kernel and
+ * `stop` immediately after it, so cudaEventElapsedTime(start, stop) is that
+ * kernel's device time.  start/stop are cudaEvent_t handles passed as void*
+ * (created by the caller); NULL, NULL clears the hook.  The paper has no
+ * counterpart; this exists for measurement only. */
+pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start, void* stop);
+
+/* Bytes of device workspace pointsht_alm / pointsht_alm_backward need for
+ * this set of catalogs (host array cats[ncat]; only n and field are read).
+ * Returns 0 and sets the last error if an argument is invalid. */
+size_t pointsht_workspace_size(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                               int32_t nfield, pointsht_precision prec);
+
+/* a_lm of each field f (Eq. alm_def):
+ *   alm_out[f] = sum_{catalogs c with field f} coeff_c sum_i w_i Y*_lm(n_i)
+ * cats: HOST array of ncat catalog descriptors (device data pointers);
+ * nfield >= 1; alm_out: device, nfield*M complex128 (2*nfield*M doubles,
+ * 16-byte aligned); workspace: device, >= pointsht_workspace_size() bytes,
+ * 256-byte aligned, contents need not be initialised and are clobbered.
+ * Every step (point preparation, the per-point recurrences, the sums over
+ * points and the final reduction) runs in this library's kernels.
+ * Errors: EINVAL on bad arguments, ENOMEM if ws_bytes is too small. */
+pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                             int32_t nfield, pointsht_precision prec, double* alm_out,
+                             void* workspace, size_t ws_bytes, void* stream);
+
+/* Poisson shot noise of each field (Sec. 2.1, last paragraphs; addition
+ * theorem with P_l(1) = 1) as the nfield x nfield matrix used by pointsht_cl:
+ *   noise_out[f*nfield + f] = sum_{c in f} coeff_c^2 sum_i w_i^2 / 4pi,
+ * off-diagonal entries 0 (catalogs of a field are disjoint point sets and
+ * different fields share no catalog).  noise_out: device, nfield*nfield
+ * doubles.  workspace: device, >= 256-byte aligned, at least
+ * 512*max(ncat,1) bytes (pointsht_workspace_size always suffices). */
+pointsht_status pointsht_shot_noise(const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                    pointsht_precision prec, double* noise_out, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
+/* Linear combination of fields (the FKP field D_b - alpha_b R of a shared
+ * random catalog, Sec. 2.1):
+ *   alm_out[o] = sum_s coef[o*nsrc + s] alm_src[s]
+ *   noise_out = C noise_src C^T, i.e. noise_out[o*nout + p] =
+ *       sum_{s,t} coef[o*nsrc+s] coef[p*nsrc+t] noise_src[s*nsrc+t]
+ * coef: device, nout*nsrc doubles; noise_src: device nsrc*nsrc (e.g. from
+ * pointsht_shot_noise), noise_out: device nout*nout; both NULL to skip. */
+pointsht_status pointsht_combine(int32_t lmax, const double* alm_src, int32_t nsrc, const double* coef,
+                                 int32_t nout, const double* noise_src, double* alm_out,
+                                 double* noise_out, void* stream);
+
+/* Pseudo-C_l (Eq. pseudoCl) of all auto and cross pairs f <= g:
+ *   C_l^{fg} = [Re(a_l0^f conj a_l0^g) + 2 sum_{m=1..l} Re(a_lm^f conj a_lm^g)] / (2l+1)
+ *              - N^{fg}
+ * alm: device nfield*M complex128; noise: device nfield*nfield doubles (the
+ * shot-noise matrix to subtract) or NULL for none; cl_out: device,
+ * npair*(lmax+1) doubles, pair index of (f, g), f <= g, in row-major upper
+ * triangle order p = f*nfield - f*(f-1)/2 + (g - f). */
+pointsht_status pointsht_cl(int32_t lmax, const double* alm, int32_t nfield, const double* noise,
+                            double* cl_out, void* stream);
+
+/* Vector-Jacobian product of pointsht_cl: given grad_cl (npair*(lmax+1)),
+ * writes grad_alm[f] = dL/dRe(a^f) + i dL/dIm(a^f) (nfield*M complex128) and,
+ * if grad_noise != NULL, grad_noise[f*nfield+g] = dL/dN^{fg}. */
+pointsht_status pointsht_cl_backward(int32_t lmax, const double* alm, int32_t nfield,
+                                     const double* grad_cl, double* grad_alm, double* grad_noise,
+                                     void* stream);
+
+/* Bandpowers C_b = sum_l theta_b^l C_l with theta_b^l = 1/Delta_l on
+ * [edges[b], edges[b+1]) (Sec. 2.1): cl: device nspec*(lmax+1); edges: device
+ * nbin+1 int32 increasing in [0, lmax+1]; out: device nspec*nbin. */
+pointsht_status pointsht_bin(int32_t lmax, const double* cl, int32_t nspec, const int32_t* edges,
+                             int32_t nbin, double* out, void* stream);
+
+/* Transpose of pointsht_bin: grad_cl[s][l] = sum_b theta_b^l grad_b[s][b]. */
+pointsht_status pointsht_bin_backward(int32_t lmax, const double* grad_b, int32_t nspec,
+                                      const int32_t* edges, int32_t nbin, double* grad_cl,
+                                      void* stream);
+
+/* Adjoint (vector-Jacobian product) of pointsht_alm with respect to the
+ * weights, plus the shot-noise term:
+ *   grad_w_c[i] = coeff_c sum_{l, m>=0} lambda_lm(x_i) Re(g^f_lm e^{i m phi_i})
+ *                 + 2 coeff_c^2 w_i gnoise_f / 4pi
+ * where g^f = grad_alm[f] (dL/dRe a + i dL/dIm a, nfield*M complex128) and
+ * gnoise_f = grad_noise[f*nfield + f] (the diagonal of dL/dN, device
+ * nfield*nfield doubles as written by pointsht_cl_backward, or NULL for 0).
+ * This is a point-evaluation synthesis that reruns the recurrence per point
+ * (derived from Eq. alm_def; the paper has no adjoint).  grad_w: HOST array of
+ * ncat device pointers, each n_c values of the dtype of w (may alias nothing
+ * else).  workspace as for pointsht_alm (pointsht_workspace_size bytes). */
+pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                      int32_t nfield, pointsht_precision prec, const double* grad_alm,
+                                      const double* grad_noise, void* const* grad_w, void* workspace,
+                                      size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POINTSHT_H */

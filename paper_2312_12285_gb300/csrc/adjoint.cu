@@ -1,0 +1,306 @@
+// adjoint.cu -- vector-Jacobian product of the point-catalog SHT with respect
+// to the weights (point-evaluation synthesis).
+//
+// From Eq. alm_def, a_lm = sum_i coeff w_i lambda_lm(x_i) e^{-i m phi_i}, so for
+// a real loss L with g_lm = dL/dRe a_lm + i dL/dIm a_lm:
+//   dL/dw_i = coeff sum_{l, m>=0} lambda_lm(x_i) Re(g_lm e^{i m phi_i}).
+// With lambda = gamma mu (see analysis.cu) the table holds gamma_lm g_lm and
+// each lane runs the same seed and mu-recurrence as the analysis for its K
+// points, accumulating sum_l mu_l (gamma g)_l in registers: no cross-lane
+// reduction.  Contributions made while a point's state is still below the
+// floating-point range (exponent block E < 0) are dropped by clearing that
+// point's accumulators when E reaches 0, and at the end of a column if it
+// never does.  Sums over m are carried in FP64 per point.
+#include "common.cuh"
+
+#include <math_constants.h>
+
+namespace psht {
+
+// Seed, phase and coefficient loads for the adjoint, from per-point values
+// held in registers (the analysis reads them from its shared-memory tile).
+namespace adj {
+
+struct F32 {
+    using real = float;
+    using real2 = float2;
+    __device__ static __forceinline__ void seed(int m, double ls, float lch, float lcl, float& mant, int& E) {
+        const float lh = (float)ls, ll = (float)(ls - (double)lh);
+        const float mf = (float)m;
+        const float pr = mf * lh;
+        float pe = fmaf(mf, lh, -pr);
+        pe = fmaf(mf, ll, pe);
+        f2 s = two_sum(pr, lch);
+        f2 e = fast_two_sum(s.hi, s.lo + pe + lcl);
+        const bool pole = e.hi < -1.0e7f;  // sin theta = 0 and m > 0: lambda_mm = 0
+        const float Ef =
+            pole ? -1048576.f : fminf(0.f, ceilf((e.hi - (float)F32Scale::CHECK_EXP) * (1.0f / F32Scale::SCALE_BITS)));
+        E = (int)Ef;
+        const float eh = pole ? 0.f : e.hi - (float)F32Scale::SCALE_BITS * Ef;
+        f2 ep = fast_two_sum(eh, pole ? 0.f : e.lo);
+        const float n = floorf(ep.hi);
+        const float fr = (ep.hi - n) + ep.lo;
+        mant = pole ? 0.f : ldexpf(exp2f(fr), (int)n);
+        if (m & 1) mant = -mant;
+    }
+    __device__ static __forceinline__ void phase(int m, uint64_t turn, float& cs, float& sn) {
+        const uint32_t t = (uint32_t)m * (uint32_t)(turn >> 32) + __umulhi((uint32_t)m, (uint32_t)turn);
+        sincospif((float)(int32_t)t * 0x1p-31f, &sn, &cs);
+    }
+    __device__ static __forceinline__ float down(float v) { return v * 0x1p-64f; }
+    __device__ static __forceinline__ float thresh() { return 0x1p-61f; }
+    __device__ static __forceinline__ void load16(const float2* g, float2 (&v)[16]) {
+        const float4* g4 = reinterpret_cast<const float4*>(g);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float4 t = __ldg(g4 + c);
+            v[2 * c] = make_float2(t.x, t.y);
+            v[2 * c + 1] = make_float2(t.z, t.w);
+        }
+    }
+    __device__ static __forceinline__ void load16a(const float* a, float (&v)[16]) {
+        const float4* a4 = reinterpret_cast<const float4*>(a);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 t = __ldg(a4 + c);
+            v[4 * c] = t.x;
+            v[4 * c + 1] = t.y;
+            v[4 * c + 2] = t.z;
+            v[4 * c + 3] = t.w;
+        }
+    }
+};
+
+struct F64 {
+    using real = double;
+    using real2 = double2;
+    __device__ static __forceinline__ void seed(int m, double ls, double lc, double, double& mant, int& E) {
+        const double e = fma((double)m, ls, lc);
+        const bool pole = e < -1.0e7;
+        const double Ef = pole ? -1048576.0 : fmin(0.0, ceil((e - (double)F64Scale::CHECK_EXP) * (1.0 / F64Scale::SCALE_BITS)));
+        E = (int)Ef;
+        const double eh = pole ? 0.0 : e - (double)F64Scale::SCALE_BITS * Ef;
+        const double n = floor(eh);
+        mant = pole ? 0.0 : ldexp(exp2(eh - n), (int)n);
+        if (m & 1) mant = -mant;
+    }
+    __device__ static __forceinline__ void phase(int m, uint64_t turn, double& cs, double& sn) {
+        const uint64_t t = (uint64_t)m * turn;
+        sincospi((double)(int64_t)t * 0x1p-63, &sn, &cs);
+    }
+    __device__ static __forceinline__ double down(double v) { return v * 0x1p-600; }
+    __device__ static __forceinline__ double thresh() { return 0x1p-200; }
+    __device__ static __forceinline__ void load16(const double2* g, double2 (&v)[16]) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __ldg(g + c);
+    }
+    __device__ static __forceinline__ void load16a(const double* a, double (&v)[16]) {
+        const double2* a2 = reinterpret_cast<const double2*>(a);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const double2 t = __ldg(a2 + c);
+            v[2 * c] = t.x;
+            v[2 * c + 1] = t.y;
+        }
+    }
+};
+
+}  // namespace adj
+
+__device__ __forceinline__ uint64_t adj_turn(double ph) {
+    double t = ph * (1.0 / (2.0 * CUDART_PI));
+    t -= floor(t);
+    if (!(t >= 0.0 && t < 1.0)) t = 0.0;
+    return __double2ull_rn(t * 18446744073709551616.0);
+}
+
+template <typename Tr, typename TIn, int K>
+__global__ void __launch_bounds__(128) adjoint_kernel(const __grid_constant__ AdjointParams p) {
+    using real = typename Tr::real;
+    using real2 = typename Tr::real2;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= p.warp0[p.ncat]) return;
+    int c = 0;
+    while (c + 1 < p.ncat && p.warp0[c + 1] <= gw) ++c;
+    const CatDesc cd = p.cat[c];
+    const int64_t base = (gw - p.warp0[c]) * (32 * K);
+    const int L = p.lmax;
+    const TIn* xs = static_cast<const TIn*>(cd.x);
+    const TIn* ps = static_cast<const TIn*>(cd.phi);
+
+    real x[K];
+    double ls[K];
+    uint64_t turn[K];
+    double tot[K];
+    bool valid[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        valid[k] = i < cd.n;
+        double xd = valid[k] ? (double)xs[i] : 0.0;
+        double ph = valid[k] ? (double)ps[i] : 0.0;
+        if (!(isfinite(xd) && isfinite(ph) && fabs(xd) <= 1.0)) {
+            if (valid[k]) atomicOr(p.err, ERR_RANGE);
+            xd = 0.0;
+            ph = 0.0;
+            valid[k] = false;
+        }
+        x[k] = (real)xd;
+        const double xr = (double)x[k];
+        const double s2 = (1.0 - xr) * (1.0 + xr);
+        ls[k] = s2 > 0.0 ? 0.5 * log2(s2) : -1.0e30;
+        turn[k] = adj_turn(ph);
+        tot[k] = 0.0;
+    }
+    const real2* gtab = static_cast<const real2*>(p.gtab) + (int64_t)cd.field * p.gstride;
+    const real* alpha_all = static_cast<const real*>(p.alpha);
+
+    for (int m = 0; m <= L; ++m) {
+        real lch, lcl;
+        if constexpr (sizeof(real) == 4) {
+            lch = p.log2c_hi[m];
+            lcl = p.log2c_lo[m];
+        } else {
+            lch = p.log2c[m];
+            lcl = 0;
+        }
+        real p1[K], p2[K], ar[K], ai[K], cs[K], sn[K];
+        int E[K];
+        bool lane_neg = false, lane_dead = true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            real mant;
+            Tr::seed(m, ls[k], lch, lcl, mant, E[k]);
+            Tr::phase(m, turn[k], cs[k], sn[k]);
+            p1[k] = real(0);
+            p2[k] = -mant;
+            ar[k] = real(0);
+            ai[k] = real(0);
+            lane_neg |= E[k] < 0;
+            lane_dead &= E[k] < 0;
+        }
+        bool any_neg = __any_sync(0xffffffffu, lane_neg);
+        bool all_dead = __all_sync(0xffffffffu, lane_dead);
+        const int64_t cs0 = p.colstart[m];
+        const real* alpha = alpha_all + cs0;
+        const real2* gcol = gtab + cs0;
+        const int len = L - m + 1;
+        const int nblk = (len + 15) >> 4;
+        for (int bk = 0; bk < nblk; ++bk) {
+            real av[16];
+            real2 gv[16];
+            Tr::load16a(alpha + 16 * bk, av);
+            Tr::load16(gcol + 16 * bk, gv);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (all_dead) {
+#pragma unroll
+                    for (int j = 8 * h; j < 8 * h + 8; ++j)
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const real mu = fma(av[j], x[k] * p1[k], -p2[k]);
+                            p2[k] = p1[k];
+                            p1[k] = mu;
+                        }
+                } else {
+#pragma unroll
+                    for (int j = 8 * h; j < 8 * h + 8; ++j)
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const real mu = fma(av[j], x[k] * p1[k], -p2[k]);
+                            p2[k] = p1[k];
+                            p1[k] = mu;
+                            ar[k] = fma(mu, gv[j].x, ar[k]);
+                            ai[k] = fma(mu, gv[j].y, ai[k]);
+                        }
+                }
+                if (any_neg) {
+                    lane_neg = false;
+                    lane_dead = true;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        if (E[k] < 0) {
+                            const real mx = fmax(fabs(p1[k]), fabs(p2[k]));
+                            if (mx > Tr::thresh()) {
+                                p1[k] = Tr::down(p1[k]);
+                                p2[k] = Tr::down(p2[k]);
+                                E[k] += 1;
+                                if (E[k] == 0) {  // drop what was summed below range
+                                    ar[k] = real(0);
+                                    ai[k] = real(0);
+                                }
+                            }
+                        }
+                        lane_neg |= E[k] < 0;
+                        lane_dead &= E[k] < 0;
+                    }
+                    any_neg = __any_sync(0xffffffffu, lane_neg);
+                    all_dead = __all_sync(0xffffffffu, lane_dead);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (E[k] == 0) tot[k] += (double)cs[k] * (double)ar[k] - (double)sn[k] * (double)ai[k];
+    }
+    const double gn = p.gnoise ? p.gnoise[(int64_t)cd.field * (p.nfield + 1)] : 0.0;
+    const TIn* ws = static_cast<const TIn*>(cd.w);
+    TIn* out = static_cast<TIn*>(p.gradw[c]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t i = base + k * 32 + lane;
+        if (i < cd.n) {
+            const double w = valid[k] ? (double)ws[i] : 0.0;
+            const double g = cd.coeff * tot[k] + 2.0 * cd.coeff * cd.coeff * w * gn / (4.0 * CUDART_PI);
+            out[i] = (TIn)g;
+        }
+    }
+}
+
+// gtab[f][colstart[m] + q] = gamma(l, m) * g^f(l, m), zero in the padding.
+template <typename R2>
+__global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const double* __restrict__ gamma,
+                                  const int64_t* __restrict__ colstart, int64_t gstride, R2* __restrict__ gtab) {
+    const int m = blockIdx.y, f = blockIdx.z;
+    const int64_t w = colstart[m + 1] - colstart[m];
+    const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < w; q += (int64_t)gridDim.x * blockDim.x) {
+        R2 v;
+        v.x = 0;
+        v.y = 0;
+        if (m + q <= L) {
+            const int64_t idx = tri_base(m, L) + m + q;
+            const double2 g = galm[(int64_t)f * M + idx];
+            const double gm = gamma[idx];
+            v.x = g.x * gm;
+            v.y = g.y * gm;
+        }
+        gtab[(int64_t)f * gstride + colstart[m] + q] = v;
+    }
+}
+
+cudaError_t launch_build_gtab(int is_f64, int L, int nfield, const double* galm, const double* gamma,
+                              const int64_t* colstart, int64_t gstride, void* gtab, cudaStream_t st) {
+    dim3 grid(4, L + 1, nfield);
+    if (is_f64)
+        build_gtab_kernel<double2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
+                                                         gstride, static_cast<double2*>(gtab));
+    else
+        build_gtab_kernel<float2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
+                                                        gstride, static_cast<float2*>(gtab));
+    return cudaGetLastError();
+}
+
+int adjoint_points_per_warp(int is_f64) { return is_f64 ? 32 * 2 : 32 * 4; }
+
+cudaError_t launch_adjoint(int is_f64, const AdjointParams& ap, cudaStream_t st) {
+    const int64_t nwarps = ap.warp0[ap.ncat];
+    if (nwarps == 0) return cudaSuccess;
+    const int64_t nblocks = (nwarps + 3) / 4;
+    if (is_f64) adjoint_kernel<adj::F64, double, 2><<<(unsigned)nblocks, 128, 0, st>>>(ap);
+    else adjoint_kernel<adj::F32, float, 4><<<(unsigned)nblocks, 128, 0, st>>>(ap);
+    return cudaGetLastError();
+}
+
+}  // namespace psht

@@ -1,0 +1,615 @@
+// api.cu -- C ABI of libpointsht (declared in include/pointsht.h).
+//
+// Host side: argument validation, the plan's recurrence tables, the workspace
+// layout and the kernel launches.  No call except pointsht_plan_create
+// allocates device memory; every kernel is enqueued on the caller's stream.
+#include "pointsht.h"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace psht {
+template <typename T>
+cudaError_t launch_prep(const PrepParams&, int, cudaStream_t);
+cudaError_t launch_analysis(const AnalysisParams&, int, int, int, cudaStream_t, int*);
+cudaError_t launch_reduce(const ReduceParams&, cudaStream_t);
+int analysis_tile_points(int, int);
+cudaError_t launch_cl(int, const double*, int, const double*, double*, cudaStream_t);
+cudaError_t launch_cl_backward(int, const double*, int, const double*, double*, double*, cudaStream_t);
+cudaError_t launch_bin(int, const double*, int, const int*, int, double*, cudaStream_t);
+cudaError_t launch_bin_backward(int, const double*, int, const int*, int, double*, cudaStream_t);
+cudaError_t launch_combine(int, const double*, int, const double*, int, const double*, double*, double*,
+                           cudaStream_t);
+cudaError_t launch_shot_noise(const PrepParams&, int, double*, int, double*, cudaStream_t);
+cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const int64_t*, int64_t, void*,
+                              cudaStream_t);
+int adjoint_points_per_warp(int);
+cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
+}  // namespace psht
+
+using namespace psht;
+
+struct pointsht_plan_s {
+    int lmax = 0;
+    int device = 0;
+    int sm_count = 0;
+    int64_t nmodes = 0;
+    int64_t acol = 0;  // colstart[lmax+1]: padded column-table length
+    void* blob = nullptr;
+    float* alpha_f = nullptr;
+    double* alpha_d = nullptr;
+    int64_t* colstart = nullptr;
+    double* gamma = nullptr;
+    float* log2c_hi = nullptr;
+    float* log2c_lo = nullptr;
+    double* log2c = nullptr;
+    unsigned* err = nullptr;
+    cudaEvent_t ev_start = nullptr;  // optional timing hook around the analysis kernel
+    cudaEvent_t ev_stop = nullptr;
+};
+
+// ------------------------------------------------------------ errors --
+static thread_local std::string g_last_error;
+
+static pointsht_status fail(pointsht_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                                  \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static constexpr int64_t SHOT_NBLK = 64;
+static constexpr int FLUSH_TILES = 16;
+
+extern "C" const char* pointsht_version(void) { return "1.0.0"; }
+extern "C" const char* pointsht_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------ tables --
+// Built in long double on the host: lambda-form recurrence coefficients
+// (App. A divided through by sqrt((2l+1)/4pi)), their gamma rescaling and
+// log2 c_m = log2 |lambda_mm| - m log2 sin(theta).
+static void build_tables(int L, std::vector<int64_t>& colstart, std::vector<float>& af, std::vector<double>& ad,
+                         std::vector<double>& gamma, std::vector<double>& l2c) {
+    colstart.assign(L + 2, 0);
+    for (int m = 0; m <= L; ++m) {
+        const int64_t len = L - m + 1;
+        colstart[m + 1] = colstart[m] + ((len + 15) / 16) * 16;
+    }
+    const int64_t acol = colstart[L + 1];
+    af.assign(acol, 0.f);
+    ad.assign(acol, 0.0);
+    const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
+    gamma.assign(M, 0.0);
+    l2c.assign(L + 1, 0.0);
+    long double sumlog = 0.0L;
+    for (int m = 0; m <= L; ++m) {
+        if (m > 0) sumlog += log2l(1.0L - 1.0L / (2.0L * m));
+        l2c[m] = (double)(0.5L * log2l((2.0L * m + 1.0L) / (4.0L * 3.141592653589793238462643383279502884L)) +
+                          0.5L * sumlog);
+        const int64_t base = tri_base(m, L);
+        std::vector<long double> g(L - m + 1, 1.0L);
+        for (int l = m + 2; l <= L; ++l) {
+            const long double ll = l, mm = m;
+            const long double B = sqrtl((2 * ll + 1) * ((ll - 1) * (ll - 1) - mm * mm) /
+                                        ((2 * ll - 3) * (ll * ll - mm * mm)));
+            g[l - m] = B * g[l - m - 2];
+        }
+        for (int l = m; l <= L; ++l) {
+            const long double ll = l, mm = m;
+            long double a = 0.0L;
+            if (l == m + 1) a = sqrtl(2 * mm + 3);
+            if (l >= m + 2) {
+                const long double A = sqrtl((4 * ll * ll - 1) / (ll * ll - mm * mm));
+                a = A * g[l - m - 1] / g[l - m];
+            }
+            af[colstart[m] + (l - m)] = (float)a;
+            ad[colstart[m] + (l - m)] = (double)a;
+            gamma[base + l] = (double)g[l - m];
+        }
+    }
+}
+
+static bool device_is_sm103(int dev, int* sms) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+    if (sms) *sms = prop.multiProcessorCount;
+    return prop.major == 10 && prop.minor == 3;
+}
+
+extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out) {
+    if (!out) return fail(POINTSHT_EINVAL, "plan_create: out is NULL");
+    *out = nullptr;
+    if (lmax < 1 || lmax > 8192) return fail(POINTSHT_EINVAL, "plan_create: lmax=%d outside [1, 8192]", lmax);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    int sms = 0;
+    if (!device_is_sm103(dev, &sms))
+        return fail(POINTSHT_EARCH, "plan_create: device %d is not compute capability 10.3 (sm_103)", dev);
+    std::vector<int64_t> colstart;
+    std::vector<float> af;
+    std::vector<double> ad, gamma, l2c;
+    build_tables(lmax, colstart, af, ad, gamma, l2c);
+    std::vector<float> lh(lmax + 1), ll(lmax + 1);
+    for (int m = 0; m <= lmax; ++m) {
+        lh[m] = (float)l2c[m];
+        ll[m] = (float)(l2c[m] - (double)lh[m]);
+    }
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t s_af = up(af.size() * 4), s_ad = up(ad.size() * 8), s_cs = up(colstart.size() * 8),
+                 s_g = up(gamma.size() * 8), s_lh = up(lh.size() * 4), s_l2 = up(l2c.size() * 8), s_err = 256;
+    const size_t total = s_af + s_ad + s_cs + s_g + 2 * s_lh + s_l2 + s_err;
+    pointsht_plan p = new pointsht_plan_s();
+    p->lmax = lmax;
+    p->device = dev;
+    p->sm_count = sms;
+    p->nmodes = (int64_t)(lmax + 1) * (lmax + 2) / 2;
+    p->acol = colstart[lmax + 1];
+    if (cudaMalloc(&p->blob, total) != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(POINTSHT_ENOMEM, "plan_create: cudaMalloc(%zu) failed", total);
+    }
+    char* b = static_cast<char*>(p->blob);
+    p->alpha_f = reinterpret_cast<float*>(b);
+    b += s_af;
+    p->alpha_d = reinterpret_cast<double*>(b);
+    b += s_ad;
+    p->colstart = reinterpret_cast<int64_t*>(b);
+    b += s_cs;
+    p->gamma = reinterpret_cast<double*>(b);
+    b += s_g;
+    p->log2c_hi = reinterpret_cast<float*>(b);
+    b += s_lh;
+    p->log2c_lo = reinterpret_cast<float*>(b);
+    b += s_lh;
+    p->log2c = reinterpret_cast<double*>(b);
+    b += s_l2;
+    p->err = reinterpret_cast<unsigned*>(b);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(p->alpha_f, af.data(), af.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->alpha_d, ad.data(), ad.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->colstart, colstart.data(), colstart.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->gamma, gamma.data(), gamma.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->log2c_hi, lh.data(), lh.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->log2c_lo, ll.data(), ll.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->log2c, l2c.data(), l2c.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, s_err);
+    if (e != cudaSuccess) {
+        cudaFree(p->blob);
+        delete p;
+        return fail(POINTSHT_ECUDA, "plan_create: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return POINTSHT_OK;
+}
+
+extern "C" void pointsht_plan_destroy(pointsht_plan plan) {
+    if (!plan) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(plan->device);
+    cudaDeviceSynchronize();
+    cudaFree(plan->blob);
+    cudaSetDevice(cur);
+    delete plan;
+}
+
+extern "C" int32_t pointsht_plan_lmax(pointsht_plan plan) { return plan ? plan->lmax : -1; }
+
+extern "C" pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start, void* stop) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_timing_events: plan is NULL");
+    if ((start == nullptr) != (stop == nullptr))
+        return fail(POINTSHT_EINVAL, "set_timing_events: start and stop must both be set or both NULL");
+    plan->ev_start = static_cast<cudaEvent_t>(start);
+    plan->ev_stop = static_cast<cudaEvent_t>(stop);
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_plan_check(pointsht_plan plan) {
+    if (!plan) return fail(POINTSHT_EINVAL, "plan_check: plan is NULL");
+    unsigned flags = 0;
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(&flags, plan->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(plan->err, 0, sizeof(unsigned)));
+    if (flags & ERR_TIMEOUT) return fail(POINTSHT_ETIMEOUT, "a bounded wait inside a kernel gave up");
+    if (flags & ERR_RANGE) return fail(POINTSHT_ERANGE, "an input point had |x| > 1 or a non-finite value");
+    if (flags & ERR_INTERNAL) return fail(POINTSHT_ECUDA, "internal kernel check failed");
+    return POINTSHT_OK;
+}
+
+// ----------------------------------------------------------- layout --
+struct Layout {
+    int is_f64 = 0;
+    int k32 = 16;       // FP32 points per lane
+    int P = 0;          // tile points
+    int narr = 0, abytes = 0;
+    int64_t chunk = 0;  // points per chunk
+    int ngroups = 0;    // m-groups
+    int64_t ntot = 0;   // prepared points
+    int64_t nunits = 0;
+    int32_t nslots = 0;
+    int64_t npad[PSHT_MAX_FIELDS] = {};
+    int64_t off[PSHT_MAX_FIELDS] = {};
+    int64_t nfpts[PSHT_MAX_FIELDS] = {};
+    int32_t nchunk[PSHT_MAX_FIELDS] = {};
+    int32_t slot0[PSHT_MAX_FIELDS] = {};
+    int64_t unit0[PSHT_MAX_FIELDS] = {};
+    // byte offsets in the workspace
+    size_t pts_off = 0, slots_off = 0, counter_off = 0, fwd_end = 0;
+    size_t gtab_off = 0, bwd_end = 0, shot_off = 0, total = 0;
+};
+
+static const int WARPS = 4;
+
+static inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static pointsht_status check_common(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                    pointsht_precision prec, const char* who) {
+    if (!plan) return fail(POINTSHT_EINVAL, "%s: plan is NULL", who);
+    if (ncat < 0 || ncat > PSHT_MAX_CATS) return fail(POINTSHT_EINVAL, "%s: ncat=%d outside [0, %d]", who, ncat, PSHT_MAX_CATS);
+    if (ncat > 0 && !cats) return fail(POINTSHT_EINVAL, "%s: cats is NULL", who);
+    if (nfield < 1 || nfield > PSHT_MAX_FIELDS)
+        return fail(POINTSHT_EINVAL, "%s: nfield=%d outside [1, %d]", who, nfield, PSHT_MAX_FIELDS);
+    if (prec != POINTSHT_FP64 && prec != POINTSHT_FP32 && prec != POINTSHT_MIXED)
+        return fail(POINTSHT_EINVAL, "%s: unknown precision %d", who, (int)prec);
+    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
+    for (int c = 0; c < ncat; ++c) {
+        const pointsht_catalog& k = cats[c];
+        if (k.n < 0) return fail(POINTSHT_EINVAL, "%s: catalog %d has n=%lld < 0", who, c, (long long)k.n);
+        if (k.field < 0 || k.field >= nfield)
+            return fail(POINTSHT_EINVAL, "%s: catalog %d has field %d outside [0, %d)", who, c, k.field, nfield);
+        if (!std::isfinite(k.coeff)) return fail(POINTSHT_EINVAL, "%s: catalog %d has a non-finite coeff", who, c);
+        if (k.n > 0) {
+            if (!k.x || !k.phi || !k.w) return fail(POINTSHT_EINVAL, "%s: catalog %d has a NULL array", who, c);
+            if (((uintptr_t)k.x | (uintptr_t)k.phi | (uintptr_t)k.w) % esz)
+                return fail(POINTSHT_EINVAL, "%s: catalog %d arrays are not %zu-byte aligned", who, c, esz);
+        }
+    }
+    return POINTSHT_OK;
+}
+
+static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                   pointsht_precision prec, Layout& lo) {
+    const int is_f64 = prec == POINTSHT_FP64;
+    lo.is_f64 = is_f64;
+    lo.k32 = 16;
+    if (const char* e = getenv("POINTSHT_K")) {
+        const int k = atoi(e);
+        if (k == 8 || k == 12 || k == 16) lo.k32 = k;
+    }
+    lo.P = analysis_tile_points(is_f64, lo.k32);
+    lo.narr = is_f64 ? 4 : 6;
+    lo.abytes = is_f64 ? 8 : 4;
+    const int L = plan->lmax;
+    lo.ngroups = (L / 2 + 1 + WARPS - 1) / WARPS;
+    for (int c = 0; c < ncat; ++c) lo.nfpts[cats[c].field] += cats[c].n;
+    int64_t ntot = 0;
+    for (int f = 0; f < nfield; ++f) {
+        lo.npad[f] = (lo.nfpts[f] + lo.P - 1) / lo.P * lo.P;
+        lo.off[f] = ntot;
+        ntot += lo.npad[f];
+    }
+    lo.ntot = ntot;
+    // Chunk size: the largest power-of-two multiple of the tile (at most
+    // 2^18 points) that still gives >= 8 units per resident CTA slot.
+    const int64_t target = (int64_t)8 * plan->sm_count * 2;
+    const int64_t cmax = (int64_t)1 << 18;
+    int64_t chunk = lo.P;
+    while (chunk * 2 <= cmax) chunk *= 2;
+    for (;;) {
+        int64_t units = 0;
+        for (int f = 0; f < nfield; ++f) units += (lo.npad[f] + chunk - 1) / chunk * lo.ngroups;
+        if (units >= target || chunk <= lo.P) break;
+        chunk /= 2;
+    }
+    lo.chunk = chunk;
+    int64_t units = 0;
+    int32_t slots = 0;
+    for (int f = 0; f < nfield; ++f) {
+        lo.nchunk[f] = (int32_t)((lo.npad[f] + chunk - 1) / chunk);
+        lo.slot0[f] = slots;
+        lo.unit0[f] = units;
+        slots += lo.nchunk[f];
+        units += (int64_t)lo.nchunk[f] * lo.ngroups;
+    }
+    lo.nslots = slots;
+    lo.nunits = units;
+    size_t b = 0;
+    lo.pts_off = b;
+    b += up256((size_t)ntot * lo.narr * lo.abytes);
+    lo.slots_off = b;
+    b += up256((size_t)slots * plan->nmodes * 16);
+    lo.counter_off = b;
+    b += 256;
+    lo.fwd_end = b;
+    lo.gtab_off = 0;
+    lo.bwd_end = up256((size_t)nfield * plan->acol * 2 * lo.abytes);
+    lo.shot_off = 0;
+    const size_t shot_end = up256((size_t)std::max(ncat, 1) * SHOT_NBLK * 8);
+    lo.total = std::max(std::max(lo.fwd_end, lo.bwd_end), shot_end);
+    return POINTSHT_OK;
+}
+
+extern "C" size_t pointsht_workspace_size(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                          int32_t nfield, pointsht_precision prec) {
+    if (check_common(plan, cats, ncat, nfield, prec, "workspace_size") != POINTSHT_OK) return 0;
+    Layout lo;
+    if (make_layout(plan, cats, ncat, nfield, prec, lo) != POINTSHT_OK) return 0;
+    return lo.total;
+}
+
+static pointsht_status check_device(pointsht_plan plan, const char* who) {
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != plan->device)
+        return fail(POINTSHT_EINVAL, "%s: current device %d differs from the plan's device %d", who, dev, plan->device);
+    return POINTSHT_OK;
+}
+
+static pointsht_status check_ws(const Layout& lo, void* ws, size_t ws_bytes, size_t need, const char* who) {
+    if (need > 0 && !ws) return fail(POINTSHT_EINVAL, "%s: workspace is NULL", who);
+    if ((uintptr_t)ws % 256) return fail(POINTSHT_EINVAL, "%s: workspace is not 256-byte aligned", who);
+    if (ws_bytes < need)
+        return fail(POINTSHT_ENOMEM, "%s: workspace has %zu bytes, %zu needed", who, ws_bytes, need);
+    (void)lo;
+    return POINTSHT_OK;
+}
+
+static void fill_prep(const pointsht_catalog* cats, int32_t ncat, int32_t nfield, const Layout& lo, void* pts,
+                      unsigned* err, PrepParams& pp) {
+    memset(&pp, 0, sizeof(pp));
+    pp.ncat = ncat;
+    pp.nfield = nfield;
+    pp.ntot = lo.ntot;
+    pp.pts = pts;
+    pp.err = err;
+    int64_t run[PSHT_MAX_FIELDS] = {};
+    for (int c = 0; c < ncat; ++c) {
+        const int f = cats[c].field;
+        pp.cat[c].x = cats[c].x;
+        pp.cat[c].phi = cats[c].phi;
+        pp.cat[c].w = cats[c].w;
+        pp.cat[c].n = cats[c].n;
+        pp.cat[c].coeff = cats[c].coeff;
+        pp.cat[c].field = f;
+        pp.cat[c].dst = lo.off[f] + run[f];
+        run[f] += cats[c].n;
+    }
+    for (int f = 0; f < nfield; ++f) {
+        pp.pad_off[f] = lo.off[f] + lo.nfpts[f];
+        pp.pad_n[f] = lo.npad[f] - lo.nfpts[f];
+    }
+}
+
+// ------------------------------------------------------------- a_lm --
+extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                        int32_t nfield, pointsht_precision prec, double* alm_out, void* workspace,
+                                        size_t ws_bytes, void* stream) {
+    pointsht_status s = check_common(plan, cats, ncat, nfield, prec, "alm");
+    if (s != POINTSHT_OK) return s;
+    if (prec == POINTSHT_MIXED)
+        return fail(POINTSHT_EINVAL, "alm: POINTSHT_MIXED is not available in this build");
+    if (prec != POINTSHT_FP64 && plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "alm: the FP32 path supports lmax <= %d (plan has %d)", F32Scale::MAX_LMAX,
+                    plan->lmax);
+    if (!alm_out || ((uintptr_t)alm_out % 16)) return fail(POINTSHT_EINVAL, "alm: alm_out NULL or not 16-byte aligned");
+    if ((s = check_device(plan, "alm")) != POINTSHT_OK) return s;
+    Layout lo;
+    make_layout(plan, cats, ncat, nfield, prec, lo);
+    if ((s = check_ws(lo, workspace, ws_bytes, lo.total, "alm")) != POINTSHT_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+
+    PrepParams pp;
+    fill_prep(cats, ncat, nfield, lo, ws + lo.pts_off, plan->err, pp);
+    if (lo.ntot > 0) {
+        cudaError_t e = lo.is_f64 ? launch_prep<double>(pp, ncat + nfield, st) : launch_prep<float>(pp, ncat + nfield, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm: prep launch: %s", cudaGetErrorString(e));
+    }
+    if (lo.nunits > 0) {
+        CUDA_TRY(cudaMemsetAsync(ws + lo.counter_off, 0, 256, st));
+        AnalysisParams ap;
+        memset(&ap, 0, sizeof(ap));
+        ap.lmax = plan->lmax;
+        ap.nfield = nfield;
+        ap.ngroups = lo.ngroups;
+        ap.flush_tiles = FLUSH_TILES;
+        ap.nmodes = plan->nmodes;
+        ap.chunk = lo.chunk;
+        ap.nunits = lo.nunits;
+        ap.ntot = lo.ntot;
+        for (int f = 0; f < nfield; ++f) {
+            ap.fld[f].off = lo.off[f];
+            ap.fld[f].npad = lo.npad[f];
+            ap.fld[f].unit0 = lo.unit0[f];
+            ap.fld[f].nchunk = lo.nchunk[f];
+            ap.fld[f].slot0 = lo.slot0[f];
+        }
+        ap.pts = ws + lo.pts_off;
+        ap.alpha_f = plan->alpha_f;
+        ap.alpha_d = plan->alpha_d;
+        ap.colstart = plan->colstart;
+        ap.log2c_hi = plan->log2c_hi;
+        ap.log2c_lo = plan->log2c_lo;
+        ap.log2c = plan->log2c;
+        ap.slots = reinterpret_cast<double*>(ws + lo.slots_off);
+        ap.counter = reinterpret_cast<int*>(ws + lo.counter_off);
+        ap.err = plan->err;
+        if (plan->ev_start) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
+        cudaError_t e = launch_analysis(ap, lo.is_f64, lo.k32, plan->sm_count, st, nullptr);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm: analysis launch: %s", cudaGetErrorString(e));
+        if (plan->ev_stop) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
+    }
+    ReduceParams rp;
+    memset(&rp, 0, sizeof(rp));
+    rp.nfield = nfield;
+    rp.nmodes = plan->nmodes;
+    for (int f = 0; f < nfield; ++f) {
+        rp.slot0[f] = lo.slot0[f];
+        rp.nchunk[f] = lo.nchunk[f];
+    }
+    rp.slots = reinterpret_cast<const double*>(ws + lo.slots_off);
+    rp.gamma = plan->gamma;
+    rp.out = alm_out;
+    cudaError_t e = launch_reduce(rp, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm: reduce launch: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+// ------------------------------------------------------- shot noise --
+extern "C" pointsht_status pointsht_shot_noise(const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                               pointsht_precision prec, double* noise_out, void* workspace,
+                                               size_t ws_bytes, void* stream) {
+    if (ncat < 0 || ncat > PSHT_MAX_CATS || (ncat > 0 && !cats))
+        return fail(POINTSHT_EINVAL, "shot_noise: bad catalog list");
+    if (nfield < 1 || nfield > PSHT_MAX_FIELDS) return fail(POINTSHT_EINVAL, "shot_noise: nfield=%d", nfield);
+    if (!noise_out) return fail(POINTSHT_EINVAL, "shot_noise: noise_out is NULL");
+    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
+    for (int c = 0; c < ncat; ++c) {
+        if (cats[c].n < 0 || cats[c].field < 0 || cats[c].field >= nfield)
+            return fail(POINTSHT_EINVAL, "shot_noise: catalog %d: bad n or field", c);
+        if (cats[c].n > 0 && (!cats[c].w || (uintptr_t)cats[c].w % esz))
+            return fail(POINTSHT_EINVAL, "shot_noise: catalog %d: w NULL or misaligned", c);
+    }
+    const size_t need = up256((size_t)std::max(ncat, 1) * SHOT_NBLK * 8);
+    if (!workspace || ws_bytes < need || (uintptr_t)workspace % 256)
+        return fail(POINTSHT_ENOMEM, "shot_noise: workspace needs %zu bytes, 256-aligned", need);
+    PrepParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.ncat = ncat;
+    pp.nfield = nfield;
+    for (int c = 0; c < ncat; ++c) {
+        pp.cat[c].w = cats[c].w;
+        pp.cat[c].n = cats[c].n;
+        pp.cat[c].coeff = cats[c].coeff;
+        pp.cat[c].field = cats[c].field;
+    }
+    cudaError_t e = launch_shot_noise(pp, prec == POINTSHT_FP64, static_cast<double*>(workspace), (int)SHOT_NBLK,
+                                      noise_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "shot_noise: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+// --------------------------------------------------- spectra & bins --
+extern "C" pointsht_status pointsht_combine(int32_t lmax, const double* alm_src, int32_t nsrc, const double* coef,
+                                            int32_t nout, const double* noise_src, double* alm_out,
+                                            double* noise_out, void* stream) {
+    if (lmax < 0 || nsrc < 1 || nout < 1 || !alm_src || !coef || !alm_out)
+        return fail(POINTSHT_EINVAL, "combine: bad arguments");
+    if ((noise_src == nullptr) != (noise_out == nullptr))
+        return fail(POINTSHT_EINVAL, "combine: noise_src and noise_out must both be set or both NULL");
+    cudaError_t e = launch_combine(lmax, alm_src, nsrc, coef, nout, noise_src, alm_out, noise_out,
+                                   static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "combine: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_cl(int32_t lmax, const double* alm, int32_t nfield, const double* noise,
+                                       double* cl_out, void* stream) {
+    if (lmax < 0 || nfield < 1 || nfield > 1024 || !alm || !cl_out) return fail(POINTSHT_EINVAL, "cl: bad arguments");
+    cudaError_t e = launch_cl(lmax, alm, nfield, noise, cl_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "cl: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_cl_backward(int32_t lmax, const double* alm, int32_t nfield,
+                                                const double* grad_cl, double* grad_alm, double* grad_noise,
+                                                void* stream) {
+    if (lmax < 0 || nfield < 1 || nfield > 1024 || !alm || !grad_cl || !grad_alm)
+        return fail(POINTSHT_EINVAL, "cl_backward: bad arguments");
+    cudaError_t e = launch_cl_backward(lmax, alm, nfield, grad_cl, grad_alm, grad_noise,
+                                       static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "cl_backward: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_bin(int32_t lmax, const double* cl, int32_t nspec, const int32_t* edges,
+                                        int32_t nbin, double* out, void* stream) {
+    if (lmax < 0 || nspec < 1 || nbin < 1 || !cl || !edges || !out) return fail(POINTSHT_EINVAL, "bin: bad arguments");
+    cudaError_t e = launch_bin(lmax, cl, nspec, edges, nbin, out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "bin: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_bin_backward(int32_t lmax, const double* grad_b, int32_t nspec,
+                                                 const int32_t* edges, int32_t nbin, double* grad_cl, void* stream) {
+    if (lmax < 0 || nspec < 1 || nbin < 1 || !grad_b || !edges || !grad_cl)
+        return fail(POINTSHT_EINVAL, "bin_backward: bad arguments");
+    cudaError_t e = launch_bin_backward(lmax, grad_b, nspec, edges, nbin, grad_cl, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "bin_backward: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+// --------------------------------------------------------- adjoint --
+extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                                 int32_t nfield, pointsht_precision prec, const double* grad_alm,
+                                                 const double* grad_noise, void* const* grad_w, void* workspace,
+                                                 size_t ws_bytes, void* stream) {
+    pointsht_status s = check_common(plan, cats, ncat, nfield, prec, "alm_backward");
+    if (s != POINTSHT_OK) return s;
+    if (prec == POINTSHT_MIXED) prec = POINTSHT_FP32;  // the adjoint has no per-m contraction to move
+    if (!grad_alm || ((uintptr_t)grad_alm % 16)) return fail(POINTSHT_EINVAL, "alm_backward: grad_alm NULL/misaligned");
+    if (ncat > 0 && !grad_w) return fail(POINTSHT_EINVAL, "alm_backward: grad_w is NULL");
+    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
+    for (int c = 0; c < ncat; ++c)
+        if (cats[c].n > 0 && (!grad_w[c] || (uintptr_t)grad_w[c] % esz))
+            return fail(POINTSHT_EINVAL, "alm_backward: grad_w[%d] NULL or misaligned", c);
+    if ((s = check_device(plan, "alm_backward")) != POINTSHT_OK) return s;
+    Layout lo;
+    make_layout(plan, cats, ncat, nfield, prec, lo);
+    if ((s = check_ws(lo, workspace, ws_bytes, lo.total, "alm_backward")) != POINTSHT_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    void* gtab = ws + lo.gtab_off;
+    cudaError_t e = launch_build_gtab(lo.is_f64, plan->lmax, nfield, grad_alm, plan->gamma, plan->colstart,
+                                      plan->acol, gtab, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: table: %s", cudaGetErrorString(e));
+    AdjointParams ap;
+    memset(&ap, 0, sizeof(ap));
+    ap.lmax = plan->lmax;
+    ap.ncat = ncat;
+    ap.nfield = nfield;
+    const int ppw = adjoint_points_per_warp(lo.is_f64);
+    int64_t wsum = 0;
+    for (int c = 0; c < ncat; ++c) {
+        ap.cat[c].x = cats[c].x;
+        ap.cat[c].phi = cats[c].phi;
+        ap.cat[c].w = cats[c].w;
+        ap.cat[c].n = cats[c].n;
+        ap.cat[c].coeff = cats[c].coeff;
+        ap.cat[c].field = cats[c].field;
+        ap.gradw[c] = grad_w[c];
+        ap.warp0[c] = wsum;
+        wsum += (cats[c].n + ppw - 1) / ppw;
+    }
+    ap.warp0[ncat] = wsum;
+    ap.gtab = gtab;
+    ap.gstride = plan->acol;
+    ap.alpha = lo.is_f64 ? static_cast<const void*>(plan->alpha_d) : static_cast<const void*>(plan->alpha_f);
+    ap.colstart = plan->colstart;
+    ap.log2c_hi = plan->log2c_hi;
+    ap.log2c_lo = plan->log2c_lo;
+    ap.log2c = plan->log2c;
+    ap.gnoise = grad_noise;
+    ap.err = plan->err;
+    e = launch_adjoint(lo.is_f64, ap, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}

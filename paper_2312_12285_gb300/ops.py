@@ -1,0 +1,305 @@
+"""PyTorch-facing calls of libpointsht.
+
+Torch supplies device memory and streams; every arithmetic step runs in the
+library's CUDA kernels through the C ABI (``include/pointsht.h``).  The
+functions here only check tensors, allocate outputs/workspace with torch and
+marshal pointers.  Complex gradients follow torch's convention
+(dL/dRe + i dL/dIm), which is also the ABI's.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+_plans: dict = {}
+_plans_lock = threading.Lock()
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """Recurrence tables for one lmax on one CUDA device (pointsht_plan)."""
+
+    def __init__(self, lmax: int, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if dev.type != "cuda":
+            raise ValueError("libpointsht runs on CUDA devices only")
+        self.lib = _lib.load()
+        self.lmax = int(lmax)
+        self.device = dev
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _lib.check(self.lib.pointsht_plan_create(self.lmax, ctypes.byref(h)), "plan_create")
+        self.handle = h
+
+    @property
+    def nmodes(self) -> int:
+        return (self.lmax + 1) * (self.lmax + 2) // 2
+
+    def check(self):
+        """Raise if a kernel recorded an error (|x| > 1, non-finite input, timeout)."""
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.pointsht_plan_check(self.handle), "plan_check")
+
+    def set_timing_events(self, start=None, stop=None):
+        """Record torch.cuda.Event start/stop around the analysis kernel of each
+        subsequent alm call (None, None clears)."""
+        s = ctypes.c_void_p(start.cuda_event) if start is not None else None
+        e = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
+        _lib.check(self.lib.pointsht_plan_set_timing_events(self.handle, s, e), "set_timing_events")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.pointsht_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def get_plan(lmax: int, device=None) -> Plan:
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    key = (dev.index if dev.index is not None else torch.cuda.current_device(), int(lmax))
+    with _plans_lock:
+        p = _plans.get(key)
+        if p is None:
+            p = Plan(lmax, torch.device("cuda", key[0]))
+            _plans[key] = p
+        return p
+
+
+@dataclass
+class Cat:
+    """One catalog on the device: x = cos(theta), phi, weights, field index and
+    coefficient (+1 data, -alpha randoms)."""
+    x: torch.Tensor
+    phi: torch.Tensor
+    w: torch.Tensor
+    field: int = 0
+    coeff: float = 1.0
+
+
+def _dtype(precision: str):
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+def _entries(cats, precision, device, weights=None):
+    dt = _dtype(precision)
+    out = []
+    for i, c in enumerate(cats):
+        w = c.w if weights is None else weights[i]
+        for name, t in (("x", c.x), ("phi", c.phi), ("w", w)):
+            if t.device != device or t.dtype != dt or not t.is_contiguous() or t.dim() != 1:
+                raise ValueError(f"catalog {i}: {name} must be a contiguous 1-D {dt} tensor on {device}")
+        if not (c.x.shape[0] == c.phi.shape[0] == w.shape[0]):
+            raise ValueError(f"catalog {i}: x, phi, w lengths differ")
+        out.append((c.x.data_ptr(), c.phi.data_ptr(), w.data_ptr(), c.x.shape[0], c.field, c.coeff))
+    return out
+
+
+def workspace_bytes(plan: Plan, cats, nfield: int, precision: str) -> int:
+    arr, n = _lib.catalog_array(_entries(cats, precision, plan.device))
+    size = plan.lib.pointsht_workspace_size(plan.handle, arr, n, nfield, _lib.PRECISIONS[precision])
+    if size == 0:
+        _lib.check(_lib.EINVAL, "workspace_size")
+    return int(size)
+
+
+def _workspace(plan, cats, nfield, precision, workspace):
+    need = workspace_bytes(plan, cats, nfield, precision)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=plan.device)
+    return workspace
+
+
+def alm_raw(plan: Plan, cats, nfield: int = 1, precision: str = "fp32", out=None, workspace=None, stream=None,
+            weights=None):
+    """a_lm of each field (pointsht_alm): complex128 tensor [nfield, M]."""
+    entries = _entries(cats, precision, plan.device, weights)
+    arr, n = _lib.catalog_array(entries)
+    workspace = _workspace(plan, cats, nfield, precision, workspace)
+    if out is None:
+        out = torch.empty((nfield, plan.nmodes), dtype=torch.complex128, device=plan.device)
+    _lib.check(plan.lib.pointsht_alm(plan.handle, arr, n, nfield, _lib.PRECISIONS[precision], _ptr(out),
+                                     _ptr(workspace), workspace.numel(), _stream_ptr(stream)), "alm")
+    return out
+
+
+def shot_noise_raw(cats, nfield: int, precision: str, device, workspace=None, stream=None, weights=None):
+    """Shot-noise matrix [nfield, nfield] (pointsht_shot_noise)."""
+    lib = _lib.load()
+    arr, n = _lib.catalog_array(_entries(cats, precision, device, weights))
+    need = 512 * max(1, n) + 256
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    out = torch.empty((nfield, nfield), dtype=torch.float64, device=device)
+    _lib.check(lib.pointsht_shot_noise(arr, n, nfield, _lib.PRECISIONS[precision], _ptr(out), _ptr(workspace),
+                                       workspace.numel(), _stream_ptr(stream)), "shot_noise")
+    return out
+
+
+def cl_raw(alm: torch.Tensor, noise=None, stream=None):
+    """Pseudo-C_l of every pair f <= g (pointsht_cl): float64 [npair, lmax+1]."""
+    lib = _lib.load()
+    nfield, M = alm.shape
+    lmax = _lmax_of(M)
+    npair = nfield * (nfield + 1) // 2
+    out = torch.empty((npair, lmax + 1), dtype=torch.float64, device=alm.device)
+    _lib.check(lib.pointsht_cl(lmax, _ptr(alm), nfield, _ptr(noise) if noise is not None else None, _ptr(out),
+                               _stream_ptr(stream)), "cl")
+    return out
+
+
+def cl_backward_raw(alm, grad_cl, want_noise=True, stream=None):
+    lib = _lib.load()
+    nfield, M = alm.shape
+    lmax = _lmax_of(M)
+    galm = torch.empty_like(alm)
+    gnoise = torch.empty((nfield, nfield), dtype=torch.float64, device=alm.device) if want_noise else None
+    _lib.check(lib.pointsht_cl_backward(lmax, _ptr(alm), nfield, _ptr(grad_cl.contiguous()), _ptr(galm),
+                                        _ptr(gnoise) if gnoise is not None else None, _stream_ptr(stream)),
+               "cl_backward")
+    return galm, gnoise
+
+
+def bin_raw(cl: torch.Tensor, edges: torch.Tensor, stream=None):
+    lib = _lib.load()
+    nspec, n = cl.shape
+    nbin = edges.shape[0] - 1
+    out = torch.empty((nspec, nbin), dtype=torch.float64, device=cl.device)
+    _lib.check(lib.pointsht_bin(n - 1, _ptr(cl), nspec, _ptr(edges), nbin, _ptr(out), _stream_ptr(stream)), "bin")
+    return out
+
+
+def bin_backward_raw(grad_b, edges, lmax, stream=None):
+    lib = _lib.load()
+    nspec, nbin = grad_b.shape
+    out = torch.empty((nspec, lmax + 1), dtype=torch.float64, device=grad_b.device)
+    _lib.check(lib.pointsht_bin_backward(lmax, _ptr(grad_b.contiguous()), nspec, _ptr(edges), nbin, _ptr(out),
+                                         _stream_ptr(stream)), "bin_backward")
+    return out
+
+
+def combine_raw(alm_src, coef, noise_src=None, stream=None):
+    """Linear combination of fields (pointsht_combine)."""
+    lib = _lib.load()
+    nsrc, M = alm_src.shape
+    nout = coef.shape[0]
+    out = torch.empty((nout, M), dtype=torch.complex128, device=alm_src.device)
+    nout_t = torch.empty((nout, nout), dtype=torch.float64, device=alm_src.device) if noise_src is not None else None
+    _lib.check(lib.pointsht_combine(_lmax_of(M), _ptr(alm_src), nsrc, _ptr(coef.contiguous()), nout,
+                                    _ptr(noise_src) if noise_src is not None else None, _ptr(out),
+                                    _ptr(nout_t) if nout_t is not None else None, _stream_ptr(stream)), "combine")
+    return out, nout_t
+
+
+def alm_backward_raw(plan, cats, nfield, precision, grad_alm, grad_noise=None, workspace=None, stream=None):
+    """d L / d w for every catalog (pointsht_alm_backward)."""
+    entries = _entries(cats, precision, plan.device)
+    arr, n = _lib.catalog_array(entries)
+    workspace = _workspace(plan, cats, nfield, precision, workspace)
+    grads = [torch.empty_like(c.w) for c in cats]
+    gw = (ctypes.c_void_p * max(1, len(grads)))(*[g.data_ptr() for g in grads])
+    _lib.check(plan.lib.pointsht_alm_backward(plan.handle, arr, n, nfield, _lib.PRECISIONS[precision],
+                                              _ptr(grad_alm.contiguous()),
+                                              _ptr(grad_noise.contiguous()) if grad_noise is not None else None,
+                                              gw, _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+               "alm_backward")
+    return grads
+
+
+def _lmax_of(M: int) -> int:
+    # (L+1)(L+2)/2 = M
+    L = int(round(((8 * M + 1) ** 0.5 - 3) / 2))
+    if (L + 1) * (L + 2) // 2 != M:
+        raise ValueError(f"{M} is not a triangle size (L+1)(L+2)/2")
+    return L
+
+
+# -------------------------------------------------------------- autograd --
+class PointSHT(torch.autograd.Function):
+    """weights of every catalog -> (a_lm [nfield, M] complex128, shot-noise matrix).
+
+    Backward runs the adjoint synthesis kernel (pointsht_alm_backward)."""
+
+    @staticmethod
+    def forward(ctx, plan, cats, nfield, precision, *weights):
+        cats2 = [Cat(c.x, c.phi, w, c.field, c.coeff) for c, w in zip(cats, weights)]
+        a = alm_raw(plan, cats2, nfield, precision)
+        noise = shot_noise_raw(cats2, nfield, precision, plan.device)
+        ctx.plan, ctx.cats, ctx.nfield, ctx.precision = plan, cats2, nfield, precision
+        return a, noise
+
+    @staticmethod
+    def backward(ctx, grad_alm, grad_noise):
+        if grad_alm is None:
+            grad_alm = torch.zeros((ctx.nfield, ctx.plan.nmodes), dtype=torch.complex128, device=ctx.plan.device)
+        grads = alm_backward_raw(ctx.plan, ctx.cats, ctx.nfield, ctx.precision, grad_alm, grad_noise)
+        return (None, None, None, None, *grads)
+
+
+class PseudoCl(torch.autograd.Function):
+    """(a_lm [nfield, M], noise [nfield, nfield] or None) -> C_l [npair, lmax+1]."""
+
+    @staticmethod
+    def forward(ctx, alm, noise):
+        ctx.save_for_backward(alm)
+        ctx.has_noise = noise is not None
+        return cl_raw(alm, noise)
+
+    @staticmethod
+    def backward(ctx, grad_cl):
+        (alm,) = ctx.saved_tensors
+        galm, gnoise = cl_backward_raw(alm, grad_cl, want_noise=ctx.has_noise)
+        return galm, gnoise
+
+
+class BinCl(torch.autograd.Function):
+    """C_l [nspec, lmax+1] -> bandpowers [nspec, nbin] (theta_b^l = 1/Delta_l)."""
+
+    @staticmethod
+    def forward(ctx, cl, edges):
+        ctx.save_for_backward(edges)
+        ctx.lmax = cl.shape[1] - 1
+        return bin_raw(cl, edges)
+
+    @staticmethod
+    def backward(ctx, grad_b):
+        (edges,) = ctx.saved_tensors
+        return bin_backward_raw(grad_b, edges, ctx.lmax), None
+
+
+def alm(cats, lmax: int, nfield: int = 1, precision: str = "fp32", plan: Plan | None = None):
+    """Differentiable a_lm and shot-noise matrix of the fields formed by ``cats``."""
+    plan = plan or get_plan(lmax, cats[0].x.device if cats else None)
+    return PointSHT.apply(plan, cats, nfield, precision, *[c.w for c in cats])
+
+
+def pseudo_cl(alm_t, noise=None):
+    return PseudoCl.apply(alm_t, noise)
+
+
+def bin_cl(cl, edges):
+    return BinCl.apply(cl, edges)
+
+
+def binned_pseudo_cl(cats, lmax: int, edges: torch.Tensor, nfield: int = 1, precision: str = "fp32",
+                     plan: Plan | None = None):
+    """Shot-noise-subtracted binned pseudo-C_l, differentiable in the weights."""
+    a, noise = alm(cats, lmax, nfield, precision, plan)
+    return bin_cl(pseudo_cl(a, noise), edges)
