@@ -4,9 +4,9 @@
 // From Eq. alm_def, a_lm = sum_i coeff w_i lambda_lm(x_i) e^{-i m phi_i}, so for
 // a real loss L with g_lm = dL/dRe a_lm + i dL/dIm a_lm:
 //   dL/dw_i = coeff sum_{l, m>=0} lambda_lm(x_i) Re(g_lm e^{i m phi_i}).
-// With lambda = gamma mu (see analysis.cu) the table holds gamma_lm g_lm and
-// each lane runs the same seed and mu-recurrence as the analysis for its K
-// points, accumulating sum_l mu_l (gamma g)_l in registers: no cross-lane
+// With lambda = gamma' sigma (see analysis.cu) the table holds gamma'_lm g_lm
+// and each lane runs the same seed and sigma-recurrence as the analysis for its
+// K points, accumulating sum_l sigma_l (gamma' g)_l in registers: no cross-lane
 // reduction.  Contributions made while a point's state is still below the
 // floating-point range (exponent block E < 0) are dropped by clearing that
 // point's accumulators when E reaches 0, and at the end of a column if it
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const __grid_constant__ Ad
             real mant;
             Tr::seed(m, ls[k], lch, lcl, mant, E[k]);
             Tr::phase(m, turn[k], cs[k], sn[k]);
-            p1[k] = real(0);
-            p2[k] = -mant;
+            p1[k] = real(0);   // sigma_{m-1}
+            p2[k] = mant;      // sigma_{m-2}: with alpha_m = 0 the first step gives sigma_m = mant
             ar[k] = real(0);
             ai[k] = real(0);
             lane_neg |= E[k] < 0;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const __grid_constant__ Ad
                     for (int j = 8 * h; j < 8 * h + 8; ++j)
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
-                            const real mu = fma(av[j], x[k] * p1[k], -p2[k]);
+                            const real mu = fma(av[j], x[k] * p1[k], p2[k]);
                             p2[k] = p1[k];
                             p1[k] = mu;
                         }
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const __grid_constant__ Ad
                     for (int j = 8 * h; j < 8 * h + 8; ++j)
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
-                            const real mu = fma(av[j], x[k] * p1[k], -p2[k]);
+                            const real mu = fma(av[j], x[k] * p1[k], p2[k]);
                             p2[k] = p1[k];
                             p1[k] = mu;
                             ar[k] = fma(mu, gv[j].x, ar[k]);

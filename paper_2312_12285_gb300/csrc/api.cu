@@ -19,6 +19,8 @@
 namespace psht {
 template <typename T>
 cudaError_t launch_prep(const PrepParams&, int, cudaStream_t);
+template <typename T>
+cudaError_t launch_prep_sorted(const SortParams&, cudaStream_t);
 cudaError_t launch_analysis(const AnalysisParams&, int, int, int, cudaStream_t, int*);
 cudaError_t launch_reduce(const ReduceParams&, cudaStream_t);
 int analysis_tile_points(int, int);
@@ -45,6 +47,7 @@ struct pointsht_plan_s {
     int64_t acol = 0;  // colstart[lmax+1]: padded column-table length
     void* blob = nullptr;
     float* alpha_f = nullptr;
+    float2* alpha_f2 = nullptr;  // (alpha, alpha) pairs for packed f32x2 arithmetic
     double* alpha_d = nullptr;
     int64_t* colstart = nullptr;
     double* gamma = nullptr;
@@ -111,17 +114,25 @@ static void build_tables(int L, std::vector<int64_t>& colstart, std::vector<floa
                                         ((2 * ll - 3) * (ll * ll - mm * mm)));
             g[l - m] = B * g[l - m - 2];
         }
+        // sigma_q = s_q mu_q with s_q = (-1)^floor(q/2), q = l - m, turns
+        // mu_l = alpha_l x mu_{l-1} - mu_{l-2} into
+        // sigma_l = (s_q/s_{q-1}) alpha_l x sigma_{l-1} + sigma_{l-2}
+        // (no negation in the inner loop); s_q is folded into gamma.
         for (int l = m; l <= L; ++l) {
             const long double ll = l, mm = m;
+            const int q = l - m;
+            const int sq = ((q >> 1) & 1) ? -1 : 1;
+            const int sq1 = q >= 1 ? ((((q - 1) >> 1) & 1) ? -1 : 1) : 1;
             long double a = 0.0L;
             if (l == m + 1) a = sqrtl(2 * mm + 3);
             if (l >= m + 2) {
                 const long double A = sqrtl((4 * ll * ll - 1) / (ll * ll - mm * mm));
                 a = A * g[l - m - 1] / g[l - m];
             }
-            af[colstart[m] + (l - m)] = (float)a;
-            ad[colstart[m] + (l - m)] = (double)a;
-            gamma[base + l] = (double)g[l - m];
+            a *= (long double)(sq * sq1);
+            af[colstart[m] + q] = (float)a;
+            ad[colstart[m] + q] = (double)a;
+            gamma[base + l] = (double)(g[q] * sq);
         }
     }
 }
@@ -152,9 +163,12 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
         ll[m] = (float)(l2c[m] - (double)lh[m]);
     }
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    std::vector<float2> af2(af.size());
+    for (size_t i = 0; i < af.size(); ++i) af2[i] = make_float2(af[i], af[i]);
+    const size_t s_af2 = up(af2.size() * 8);
     const size_t s_af = up(af.size() * 4), s_ad = up(ad.size() * 8), s_cs = up(colstart.size() * 8),
                  s_g = up(gamma.size() * 8), s_lh = up(lh.size() * 4), s_l2 = up(l2c.size() * 8), s_err = 256;
-    const size_t total = s_af + s_ad + s_cs + s_g + 2 * s_lh + s_l2 + s_err;
+    const size_t total = s_af + s_af2 + s_ad + s_cs + s_g + 2 * s_lh + s_l2 + s_err;
     pointsht_plan p = new pointsht_plan_s();
     p->lmax = lmax;
     p->device = dev;
@@ -169,6 +183,8 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     char* b = static_cast<char*>(p->blob);
     p->alpha_f = reinterpret_cast<float*>(b);
     b += s_af;
+    p->alpha_f2 = reinterpret_cast<float2*>(b);
+    b += s_af2;
     p->alpha_d = reinterpret_cast<double*>(b);
     b += s_ad;
     p->colstart = reinterpret_cast<int64_t*>(b);
@@ -184,6 +200,7 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     p->err = reinterpret_cast<unsigned*>(b);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(p->alpha_f, af.data(), af.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->alpha_f2, af2.data(), af2.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->alpha_d, ad.data(), ad.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->colstart, colstart.data(), colstart.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->gamma, gamma.data(), gamma.size() * 8, cudaMemcpyHostToDevice);
@@ -237,7 +254,7 @@ extern "C" pointsht_status pointsht_plan_check(pointsht_plan plan) {
 // ----------------------------------------------------------- layout --
 struct Layout {
     int is_f64 = 0;
-    int k32 = 16;       // FP32 points per lane
+    int k32 = 116;      // FP32 kernel variant (see analysis_tile_points)
     int P = 0;          // tile points
     int narr = 0, abytes = 0;
     int64_t chunk = 0;  // points per chunk
@@ -252,7 +269,8 @@ struct Layout {
     int32_t slot0[PSHT_MAX_FIELDS] = {};
     int64_t unit0[PSHT_MAX_FIELDS] = {};
     // byte offsets in the workspace
-    size_t pts_off = 0, slots_off = 0, counter_off = 0, fwd_end = 0;
+    size_t pts_off = 0, slots_off = 0, counter_off = 0, hist_off = 0, fwd_end = 0;
+    int64_t nranges = 0;
     size_t gtab_off = 0, bwd_end = 0, shot_off = 0, total = 0;
 };
 
@@ -289,10 +307,10 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
                                    pointsht_precision prec, Layout& lo) {
     const int is_f64 = prec == POINTSHT_FP64;
     lo.is_f64 = is_f64;
-    lo.k32 = 16;
+    lo.k32 = 116;
     if (const char* e = getenv("POINTSHT_K")) {
         const int k = atoi(e);
-        if (k == 8 || k == 12 || k == 16) lo.k32 = k;
+        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116) lo.k32 = k;
     }
     lo.P = analysis_tile_points(is_f64, lo.k32);
     lo.narr = is_f64 ? 4 : 6;
@@ -338,6 +356,10 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     b += up256((size_t)slots * plan->nmodes * 16);
     lo.counter_off = b;
     b += 256;
+    lo.nranges = 0;
+    for (int c = 0; c < ncat; ++c) lo.nranges += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
+    lo.hist_off = b;
+    b += up256((size_t)std::max<int64_t>(lo.nranges, 1) * SORT_BUCKETS * 8);
     lo.fwd_end = b;
     lo.gtab_off = 0;
     lo.bwd_end = up256((size_t)nfield * plan->acol * 2 * lo.abytes);
@@ -420,7 +442,18 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
     PrepParams pp;
     fill_prep(cats, ncat, nfield, lo, ws + lo.pts_off, plan->err, pp);
     if (lo.ntot > 0) {
-        cudaError_t e = lo.is_f64 ? launch_prep<double>(pp, ncat + nfield, st) : launch_prep<float>(pp, ncat + nfield, st);
+        SortParams sp;
+        memset(&sp, 0, sizeof(sp));
+        sp.prep = pp;
+        int64_t r = 0;
+        for (int c = 0; c < ncat; ++c) {
+            sp.range0[c] = r;
+            r += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
+        }
+        sp.range0[ncat] = r;
+        for (int f = 0; f < nfield; ++f) sp.field_off[f] = lo.off[f];
+        sp.hist = reinterpret_cast<int64_t*>(ws + lo.hist_off);
+        cudaError_t e = lo.is_f64 ? launch_prep_sorted<double>(sp, st) : launch_prep_sorted<float>(sp, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm: prep launch: %s", cudaGetErrorString(e));
     }
     if (lo.nunits > 0) {
@@ -444,6 +477,7 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
         }
         ap.pts = ws + lo.pts_off;
         ap.alpha_f = plan->alpha_f;
+        ap.alpha_f2 = plan->alpha_f2;
         ap.alpha_d = plan->alpha_d;
         ap.colstart = plan->colstart;
         ap.log2c_hi = plan->log2c_hi;

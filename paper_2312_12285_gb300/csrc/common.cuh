@@ -60,6 +60,7 @@ struct AnalysisParams {
     FieldDesc fld[PSHT_MAX_FIELDS];
     const void* pts;        // prepared points, SoA with stride ntot
     const float* alpha_f;   // padded columns, FP32
+    const float2* alpha_f2; // padded columns, FP32 (alpha, alpha) pairs
     const double* alpha_d;  // padded columns, FP64
     const int64_t* colstart;
     const float* log2c_hi;  // log2 c_m as float pair
@@ -68,6 +69,9 @@ struct AnalysisParams {
     double* slots;          // [slot][nmodes][2]
     int* counter;
     unsigned* err;
+#ifdef __CUDACC__
+    __device__ __forceinline__ const float2* alpha2_col(int m) const { return alpha_f2 + colstart[m]; }
+#endif
 };
 
 struct CatDesc {
@@ -89,6 +93,16 @@ struct PrepParams {
     int64_t pad_n[PSHT_MAX_FIELDS];
     void* pts;
     unsigned* err;
+};
+
+#define SORT_BUCKETS 256
+#define SORT_RANGE 4096  // points per CTA range of the counting sort
+
+struct SortParams {
+    PrepParams prep;                     // catalogs (dst unused), pads, output
+    int64_t range0[PSHT_MAX_CATS + 1];   // first CTA range of each catalog
+    int64_t field_off[PSHT_MAX_FIELDS];  // first prepared point of each field
+    int64_t* hist;                       // [nranges][SORT_BUCKETS] counts, then offsets
 };
 
 struct ReduceParams {
