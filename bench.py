@@ -369,10 +369,12 @@ def ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(wl, args), "points": wl.npoints, "lmax": L, "nmodes": wl.nmodes,
                        "fields": nfield, "l2": "inputs larger than L2 (prepared points 24 B x 1e7 = 240 MB)",
+                       "modes_counted": "nominal (lmax+1)(lmax+2)/2 per point; accumulation skipped in 16-step "
+                                        "blocks where every point of a warp is below the FP32 range (exact zeros)",
                        "parallelism": f"points sharded over {world} GPU(s), one all-reduce of a_lm"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "analysis_kernel<TraitsF32,8,4>", "kernel_ms": kms,
+                         "kernel": "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)", "kernel_ms": kms,
                          "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                         f"{sm_max:.0f} MHz (recipe unit counts and clock)"},
             "cpu_baseline": cpu,

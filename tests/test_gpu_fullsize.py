@@ -1,0 +1,83 @@
+"""Parity at the benchmark's full size and launch configuration: 1e6 lognormal
+galaxies + 9e6 randoms in the cap mask, lmax 2048, FP32 path, through the C
+ABI exactly as bench.py calls it.  The oracle cannot finish the whole
+triangle in seconds, so it computes whole m-columns over all 1e7 points:
+m = 0 (largest values, strongest data - alpha * randoms cancellation at low
+l), and the short columns m = 1900, 2047, 2048 (deepest below-range seeds).
+
+Tolerance: relative L2 error of each column <= 1e-5 (FP32 recurrence with
+FP64-accurate seeds and phases), except m = 0 (see below)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2312_12285_gb300 import catalogs, ops  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    wl = catalogs.config(3)
+    cats = [ops.Cat(torch.from_numpy(c.x).to(dev), torch.from_numpy(c.phi).to(dev), torch.from_numpy(c.w).to(dev),
+                    c.field, c.coeff) for c in wl.catalogs]
+    plan = ops.get_plan(wl.lmax, dev)
+    a = ops.alm_raw(plan, cats, 1, "fp32")
+    torch.cuda.synchronize()
+    plan.check()
+    return wl, a.cpu().numpy()[0]
+
+
+def test_fullsize_sampled_columns(run):
+    wl, a = run
+    L = wl.lmax
+    x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
+    phi = np.concatenate([c.phi.astype(np.float64) for c in wl.catalogs])
+    w = np.concatenate([c.w.astype(np.float64) * c.coeff for c in wl.catalogs])
+    assert x.shape[0] == 10_000_000
+    # m = 0 carries the points near the pole, where lambda_l0 is largest and
+    # the FP32 recurrence error grows to ~1e-3 of lambda_max by l ~ 2048 (the
+    # FP32 error model; reproduced by a float32 emulation): measured column
+    # error 1.3e-4.  Its weight in C_l is 1/(2l+1), far below the C_l target.
+    tol = {0: 3e-4, 1900: 1e-5, 2047: 1e-5, 2048: 1e-5}
+    ref = oracle.alm(x, phi, w, L, mlist=list(tol))
+    for m in tol:
+        col = a[oracle.index(m, m, L):oracle.index(L, m, L) + 1]
+        err = np.linalg.norm(col - ref[m]) / np.linalg.norm(ref[m])
+        assert err <= tol[m], (m, err)
+
+
+def test_fullsize_monopole_and_dipole_exact_sums(run):
+    """a_00 = sum_i s_i w_i / sqrt(4 pi) and a_10 = sqrt(3/4pi) sum_i s_i w_i x_i
+    hold at any size (closed forms of Y_00 and Y_10)."""
+    wl, a = run
+    x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
+    w = np.concatenate([c.w.astype(np.float64) * c.coeff for c in wl.catalogs])
+    a00 = np.sum(w) / np.sqrt(4 * np.pi)
+    a10 = np.sqrt(3 / (4 * np.pi)) * np.sum(w * x)
+    scale = np.sqrt(np.sum(w * w) / (4 * np.pi))  # typical |a_lm| (shot-noise level)
+    assert abs(a[0] - a00) <= 1e-5 * scale
+    assert abs(a[1] - a10) <= 1e-5 * scale
+
+
+def test_fullsize_low_l_pseudo_cl(run):
+    """Full-size C_l for 1 <= l <= 32, where the window is largest and the
+    data - alpha * randoms cancellation strongest: the oracle transforms all
+    1e7 points to lmax 32 (a_lm for l <= 32 does not depend on lmax)."""
+    wl, a = run
+    L = wl.lmax
+    Ls = 32
+    x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
+    phi = np.concatenate([c.phi.astype(np.float64) for c in wl.catalogs])
+    w = np.concatenate([c.w.astype(np.float64) * c.coeff for c in wl.catalogs])
+    ref = oracle.alm(x, phi, w, Ls)
+    sub = np.concatenate([a[oracle.index(m, m, L):oracle.index(Ls, m, L) + 1] for m in range(Ls + 1)])
+    tot = oracle.cl(ref, ref, Ls)
+    got = oracle.cl(sub, sub, Ls)
+    err = float(np.max(np.abs(got[1:] - tot[1:]) / tot[1:]))
+    assert err <= 1e-5, err
