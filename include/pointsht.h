@@ -200,6 +200,29 @@ pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog
                                       const double* grad_noise, void* const* grad_w, void* workspace,
                                       size_t ws_bytes, void* stream);
 
+/* Size of the fixed scratch array used by pointsht_alm_noalloc (64 MiB). */
+#define POINTSHT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* pointsht_alm for callers that cannot allocate device memory (the paper has
+ * no counterpart: this exists for callers such as host frameworks that own
+ * every device allocation, or pipelines that forbid allocation once running,
+ * and so cannot provide a workspace).  Same arguments and results as
+ * pointsht_alm minus the workspace: the scratch is a fixed array of
+ * POINTSHT_NOALLOC_SCRATCH_BYTES inside the library's device image, held by
+ * every GPU that loads the library until the process exits.  The call itself
+ * performs no allocation of any kind.
+ * - Limit: returns ENOMEM (nothing enqueued) when pointsht_workspace_size()
+ *   for these catalogs exceeds POINTSHT_NOALLOC_SCRATCH_BYTES (roughly lmax
+ *   <= 512 with up to ~1e6 points; larger problems need pointsht_alm).
+ * - The first call on a device looks up the array's device address on that
+ *   device (make it before any stream capture); later calls reuse it.
+ * - All calls share the one array and it keeps the last call's contents;
+ *   everything the transform needs to start at zero is cleared by the call.
+ *   Calls whose work overlaps on the GPU (different streams, or different host
+ *   threads without ordering) race on the array: serialise them. */
+pointsht_status pointsht_alm_noalloc(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                     int32_t nfield, pointsht_precision prec, double* alm_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

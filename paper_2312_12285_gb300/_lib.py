@@ -23,7 +23,7 @@ EXPORTS = (
     "pointsht_plan_lmax", "pointsht_plan_check", "pointsht_plan_set_timing_events", "pointsht_workspace_size",
     "pointsht_alm",
     "pointsht_shot_noise", "pointsht_combine", "pointsht_cl", "pointsht_cl_backward", "pointsht_bin",
-    "pointsht_bin_backward", "pointsht_alm_backward",
+    "pointsht_bin_backward", "pointsht_alm_backward", "pointsht_alm_noalloc",
 )
 
 
@@ -73,6 +73,7 @@ def load(build_if_missing: bool = True):
             "pointsht_bin_backward": ([i32, dp, i32, vp, i32, dp, vp], ctypes.c_int),
             "pointsht_alm_backward": ([vp, cp, i32, i32, ctypes.c_int, dp, dp, ctypes.POINTER(vp), vp, sz, vp],
                                       ctypes.c_int),
+            "pointsht_alm_noalloc": ([vp, cp, i32, i32, ctypes.c_int, dp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

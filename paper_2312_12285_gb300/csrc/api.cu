@@ -72,6 +72,9 @@ static pointsht_status fail(pointsht_status s, const char* fmt, ...) {
     return s;
 }
 
+// Sets the thread's last-error message (used by other translation units).
+pointsht_status psht_set_error(pointsht_status s, const char* msg) { return fail(s, "%s", msg); }
+
 #define CUDA_TRY(call)                                                                                  \
     do {                                                                                                \
         cudaError_t e_ = (call);                                                                        \
