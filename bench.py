@@ -128,11 +128,6 @@ def profiled_traffic(workload: str, npoints: int):
     return per_pt * npoints
 
 
-def shard(arr, rank, world):
-    n = arr.shape[0]
-    return arr[n * rank // world: n * (rank + 1) // world]
-
-
 def load_workload(args):
     from paper_2312_12285_gb300 import catalogs
     wl = catalogs.config(args.config, scale=args.scale, lmax=args.lmax)
@@ -215,6 +210,7 @@ def ours(args):
     import torch
 
     from paper_2312_12285_gb300 import catalogs, ops
+    from paper_2312_12285_gb300.sharding import allreduce_sum, shard_array as shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,8 +241,7 @@ def ours(args):
         a = ops.alm_raw(plan, cs, nfield, prec, out=out, workspace=ws)
         noise = ops.shot_noise_raw(cs, nfield, prec, dev, workspace=ws)
         if dist is not None:
-            dist.all_reduce(torch.view_as_real(a))
-            dist.all_reduce(noise)
+            allreduce_sum([a, noise])
         cl = ops.cl_raw(a, noise)
         cb = ops.bin_raw(cl, edges)
         return cl, cb
