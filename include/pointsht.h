@@ -115,6 +115,15 @@ pointsht_status pointsht_plan_check(pointsht_plan plan);
  * counterpart; this exists for measurement only. */
 pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start, void* stop);
 
+/* Tuning of the FP32 analysis kernel for this plan (the paper has no
+ * counterpart; chosen by the autotuner): variant 0 = library default, or
+ * 8 / 12 / 16 = points per lane with scalar FMAs, 116 = 16 points per lane as
+ * f32x2 pairs, 108 = four warps sharing each order pair's accumulator;
+ * chunk_log2 0 = automatic, else log2 of the points per accumulation chunk
+ * (10..22).  Changes the workspace size: query pointsht_workspace_size after
+ * setting.  EINVAL for values outside these sets. */
+pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, int32_t chunk_log2);
+
 /* Bytes of device workspace pointsht_alm / pointsht_alm_backward need for
  * this set of catalogs (host array cats[ncat]; only n and field are read).
  * Returns 0 and sets the last error if an argument is invalid. */

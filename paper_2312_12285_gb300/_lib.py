@@ -20,7 +20,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "mixed": MIXED}
 
 EXPORTS = (
     "pointsht_version", "pointsht_last_error", "pointsht_plan_create", "pointsht_plan_destroy",
-    "pointsht_plan_lmax", "pointsht_plan_check", "pointsht_plan_set_timing_events", "pointsht_workspace_size",
+    "pointsht_plan_lmax", "pointsht_plan_check", "pointsht_plan_set_timing_events", "pointsht_plan_set_tuning",
+    "pointsht_workspace_size",
     "pointsht_alm",
     "pointsht_shot_noise", "pointsht_combine", "pointsht_cl", "pointsht_cl_backward", "pointsht_bin",
     "pointsht_bin_backward", "pointsht_alm_backward", "pointsht_alm_noalloc",
@@ -63,6 +64,7 @@ def load(build_if_missing: bool = True):
             "pointsht_plan_lmax": ([vp], i32),
             "pointsht_plan_check": ([vp], ctypes.c_int),
             "pointsht_plan_set_timing_events": ([vp, vp, vp], ctypes.c_int),
+            "pointsht_plan_set_tuning": ([vp, i32, i32], ctypes.c_int),
             "pointsht_workspace_size": ([vp, cp, i32, i32, ctypes.c_int], sz),
             "pointsht_alm": ([vp, cp, i32, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_shot_noise": ([cp, i32, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),

@@ -29,6 +29,10 @@
 
 #include <math_constants.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace psht {
 
 // ====================================================================
@@ -1215,10 +1219,8 @@ template <int K, int G, int WG>
 cudaError_t launch_analysis_f32g(const AnalysisParams& ap, int sm_count, cudaStream_t st, int* grid_out) {
     const size_t smem = analysis_f32g_smem_bytes<K, G, WG>(ap.lmax);
     auto kern = analysis_f32g_kernel<K, G, WG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G * WG * 32, smem);
+    cudaError_t e = configure_once(kern, G * WG * 32, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * occ;
@@ -1288,6 +1290,32 @@ cudaError_t launch_prep_sorted(const SortParams& sp, cudaStream_t st) {
 template cudaError_t launch_prep_sorted<float>(const SortParams&, cudaStream_t);
 template cudaError_t launch_prep_sorted<double>(const SortParams&, cudaStream_t);
 
+// Occupancy of a kernel at a dynamic shared-memory size, with the attribute
+// raised once per (device, kernel, size).  Cached so that calls made while a
+// stream is being captured into a CUDA graph only enqueue kernels.
+template <typename KernelT>
+cudaError_t configure_once(KernelT kern, int threads, size_t smem, int* occ_out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({dev, smem});
+    if (it != cache.end()) {
+        *occ_out = it->second;
+        return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    cache[{dev, smem}] = occ;
+    *occ_out = occ;
+    return cudaSuccess;
+}
+
 template <typename Tr, int K, int W>
 size_t analysis_smem_bytes(int lmax) {
     const int accw = (lmax + 2 + 3) & ~3;
@@ -1299,10 +1327,8 @@ template <typename Tr, int K, int W, bool PACKED = false>
 cudaError_t launch_analysis_t(const AnalysisParams& ap, int sm_count, cudaStream_t st, int* grid_out) {
     const size_t smem = analysis_smem_bytes<Tr, K, W>(ap.lmax);
     auto kern = analysis_kernel<Tr, K, W, PACKED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, W * 32, smem);
+    cudaError_t e = configure_once(kern, W * 32, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * occ;

@@ -57,6 +57,8 @@ struct pointsht_plan_s {
     unsigned* err = nullptr;
     cudaEvent_t ev_start = nullptr;  // optional timing hook around the analysis kernel
     cudaEvent_t ev_stop = nullptr;
+    int variant = 0;     // FP32 analysis kernel variant (0 = default)
+    int chunk_log2 = 0;  // points per accumulation chunk (0 = automatic)
 };
 
 // ------------------------------------------------------------ errors --
@@ -242,6 +244,17 @@ extern "C" pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, v
     return POINTSHT_OK;
 }
 
+extern "C" pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, int32_t chunk_log2) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_tuning: plan is NULL");
+    if (!(variant == 0 || variant == 8 || variant == 12 || variant == 16 || variant == 108 || variant == 116))
+        return fail(POINTSHT_EINVAL, "set_tuning: unknown variant %d", variant);
+    if (!(chunk_log2 == 0 || (chunk_log2 >= 10 && chunk_log2 <= 22)))
+        return fail(POINTSHT_EINVAL, "set_tuning: chunk_log2 %d outside {0} or [10, 22]", chunk_log2);
+    plan->variant = variant;
+    plan->chunk_log2 = chunk_log2;
+    return POINTSHT_OK;
+}
+
 extern "C" pointsht_status pointsht_plan_check(pointsht_plan plan) {
     if (!plan) return fail(POINTSHT_EINVAL, "plan_check: plan is NULL");
     unsigned flags = 0;
@@ -315,6 +328,7 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
         const int k = atoi(e);
         if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116) lo.k32 = k;
     }
+    if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
     lo.narr = is_f64 ? 4 : 6;
     lo.abytes = is_f64 ? 8 : 4;
@@ -340,6 +354,7 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
         if (units >= target || chunk <= lo.P) break;
         chunk /= 2;
     }
+    if (plan->chunk_log2) chunk = std::max<int64_t>((int64_t)1 << plan->chunk_log2, lo.P);
     lo.chunk = chunk;
     int64_t units = 0;
     int32_t slots = 0;

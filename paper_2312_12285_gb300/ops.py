@@ -60,6 +60,11 @@ class Plan:
         e = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
         _lib.check(self.lib.pointsht_plan_set_timing_events(self.handle, s, e), "set_timing_events")
 
+    def set_tuning(self, variant: int = 0, chunk_log2: int = 0):
+        """FP32 analysis kernel variant and accumulation chunk size (0 = defaults)."""
+        _lib.check(self.lib.pointsht_plan_set_tuning(self.handle, int(variant), int(chunk_log2)), "set_tuning")
+        self.tuning = (int(variant), int(chunk_log2))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.pointsht_plan_destroy(self.handle)
@@ -303,3 +308,52 @@ def binned_pseudo_cl(cats, lmax: int, edges: torch.Tensor, nfield: int = 1, prec
     """Shot-noise-subtracted binned pseudo-C_l, differentiable in the weights."""
     a, noise = alm(cats, lmax, nfield, precision, plan)
     return bin_cl(pseudo_cl(a, noise), edges)
+
+
+# ------------------------------------------------------------ CUDA graphs --
+class GraphStep:
+    """Capture one call of ``fn`` (a function that only enqueues work through
+    this library on the current stream, with fixed input buffers) into a CUDA
+    graph and replay it.  ``fn`` is run ``warmup`` times first so that kernel
+    attributes are configured outside the capture."""
+
+    def __init__(self, fn, warmup: int = 2):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.out = fn()
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
+
+
+def make_pipeline(plan: Plan, cats, nsrc: int, precision: str = "fp32", coef=None, edges=None):
+    """One pass of the hot path as a function of fixed device buffers, ready
+    for CUDA-graph capture: a_lm of the ``nsrc`` source fields in one
+    persistent launch, their shot-noise matrix, the optional combination into
+    fields ``coef`` [nout, nsrc] (the FKP fields D_b - alpha_b R of a shared
+    random catalog, Sec. 2.1), all auto and cross pseudo-C_l, and optional
+    bandpowers.  Returns fn() -> (C_l [npair, lmax+1], C_b or None)."""
+    dev = plan.device
+    ws = torch.empty(workspace_bytes(plan, cats, nsrc, precision), dtype=torch.uint8, device=dev)
+    a_buf = torch.empty((nsrc, plan.nmodes), dtype=torch.complex128, device=dev)
+    nws = torch.empty(512 * max(1, len(cats)) + 256, dtype=torch.uint8, device=dev)
+    coef = None if coef is None else coef.to(device=dev, dtype=torch.float64).contiguous()
+
+    def fn():
+        a = alm_raw(plan, cats, nsrc, precision, out=a_buf, workspace=ws)
+        noise = shot_noise_raw(cats, nsrc, precision, dev, workspace=nws)
+        if coef is not None:
+            a, noise = combine_raw(a, coef, noise)
+        cl = cl_raw(a, noise)
+        cb = bin_raw(cl, edges) if edges is not None else None
+        return cl, cb
+
+    return fn
