@@ -37,7 +37,7 @@ def _loss_and_grads(dev, wl, edges, gb):
     loss = (cb[0] * torch.from_numpy(gb).to(dev)).sum()
     loss.backward()
     torch.cuda.synchronize()
-    return cats, float(loss), cb
+    return cats, float(loss.detach()), cb
 
 
 def test_gradient_lmax1024_vs_oracle(dev):
