@@ -107,10 +107,10 @@ int32_t pointsht_plan_lmax(pointsht_plan plan);
  * OK otherwise. */
 pointsht_status pointsht_plan_check(pointsht_plan plan);
 
-/* Timing hook: while set, every pointsht_alm call on this plan records
- * `start` on its stream immediately before launching the analysis kernel and
- * `stop` immediately after it, so cudaEventElapsedTime(start, stop) is that
- * kernel's device time.  start/stop are cudaEvent_t handles passed as void*
+/* Timing hook: while set, every pointsht_alm (and pointsht_alm_columns) call
+ * on this plan records `start` on its stream immediately before launching the
+ * analysis kernel(s) and `stop` immediately after, so
+ * cudaEventElapsedTime(start, stop) is their device time.  start/stop are cudaEvent_t handles passed as void*
  * (created by the caller); NULL, NULL clears the hook.  The paper has no
  * counterpart; this exists for measurement only. */
 pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start, void* stop);
@@ -208,6 +208,33 @@ pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog
                                       int32_t nfield, pointsht_precision prec, const double* grad_alm,
                                       const double* grad_noise, void* const* grad_w, void* workspace,
                                       size_t ws_bytes, void* stream);
+
+/* ---- Weight columns on one point set ----------------------------------
+ * F weight columns on the same n points (for example per-bin weights on a
+ * shared random catalog, systematics or jackknife weights):
+ *   alm_out[f] = sum_i w[f*n + i] Y*_lm(n_i),   f = 0..ncol-1   (Eq. alm_def)
+ * For one order m this is the contraction a_m[l, f] = sum_i lambda_lm(x_i)
+ * W_m[i, f] with W_m[i, f] = w_f,i e^{-i m phi_i}: the recurrence runs once per
+ * point for all columns.
+ * - POINTSHT_MIXED: lambda_lm from the FP32 recurrence; the contraction runs on
+ *   the tensor cores with both operands split into fp16 hi + lo parts
+ *   (hi*hi + lo*hi + hi*lo, FP32 accumulation, FP64 sums over chunks).  Each
+ *   column is scaled by a power of two so that max|w| lies in [1, 2) (exact,
+ *   undone in FP64).  Up to 4 columns share one pass; more columns take
+ *   further passes over the prepared points.  lmax is limited by the shared
+ *   memory of one CTA (EINVAL beyond, about lmax 3100 on sm_103).
+ * - POINTSHT_FP32: the same result through pointsht_alm with one catalog and
+ *   field per column (the plain FP32 path, for comparison).
+ * x, phi: device, n floats; w: device, ncol*n floats (column-major: column f
+ * at w + f*n); alm_out: device, ncol*M complex128, 16-byte aligned;
+ * workspace: device, >= pointsht_workspace_size_columns() bytes, 256-byte
+ * aligned, clobbered.  1 <= ncol <= 64.  Errors as for pointsht_alm;
+ * non-finite x, phi, w or |x| > 1 set the ERANGE flag (the point is dropped). */
+size_t pointsht_workspace_size_columns(pointsht_plan plan, int64_t n, int32_t ncol, pointsht_precision prec);
+
+pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const float* phi, const float* w,
+                                     int64_t n, int32_t ncol, pointsht_precision prec, double* alm_out,
+                                     void* workspace, size_t ws_bytes, void* stream);
 
 /* Size of the fixed scratch array used by pointsht_alm_noalloc (64 MiB). */
 #define POINTSHT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)

@@ -285,6 +285,26 @@ def tomographic(nbins: int, n_min: float, n_max: float, n_ran: int, lmax: int, c
                     {"alpha": alpha, "nbins": nbins, "mask": mask})
 
 
+def weight_columns(wl: Workload, ncol: int):
+    """One point set (all catalogs of field 0 concatenated) carrying ``ncol``
+    weight columns, as jackknife resampling of a pseudo-C_l uses them:
+    column 0 is the field's signed weights coeff_c * w_i (data - alpha
+    randoms); column k >= 1 is the same with the k-th of ncol - 1 equal
+    azimuthal wedges removed (weights set to 0).  Returns float32 x, phi [n]
+    and W [ncol, n]."""
+    cats = [c for c in wl.catalogs if c.field == 0]
+    x = np.concatenate([c.x for c in cats]).astype(np.float32)
+    phi = np.concatenate([c.phi for c in cats]).astype(np.float32)
+    w0 = np.concatenate([c.w.astype(np.float64) * c.coeff for c in cats]).astype(np.float32)
+    W = np.empty((ncol, x.shape[0]), np.float32)
+    W[0] = w0
+    nw = max(1, ncol - 1)
+    wedge = np.floor(np.mod(phi.astype(np.float64), 2.0 * math.pi) / (2.0 * math.pi) * nw).astype(np.int64)
+    for k in range(1, ncol):
+        W[k] = np.where(wedge == k - 1, np.float32(0.0), w0)
+    return x, phi, W
+
+
 def log_bin_edges(lmax: int, nbins: int = 32) -> np.ndarray:
     """Log-spaced multipole bin edges e_k = floor(2 (N_l/2)^(k/nbins)), made
     strictly increasing, with the last edge = lmax + 1."""

@@ -25,27 +25,11 @@ struct F32 {
     using real = float;
     using real2 = float2;
     __device__ static __forceinline__ void seed(int m, double ls, float lch, float lcl, float& mant, int& E) {
-        const float lh = (float)ls, ll = (float)(ls - (double)lh);
-        const float mf = (float)m;
-        const float pr = mf * lh;
-        float pe = fmaf(mf, lh, -pr);
-        pe = fmaf(mf, ll, pe);
-        f2 s = two_sum(pr, lch);
-        f2 e = fast_two_sum(s.hi, s.lo + pe + lcl);
-        const bool pole = e.hi < -1.0e7f;  // sin theta = 0 and m > 0: lambda_mm = 0
-        const float Ef =
-            pole ? -1048576.f : fminf(0.f, ceilf((e.hi - (float)F32Scale::CHECK_EXP) * (1.0f / F32Scale::SCALE_BITS)));
-        E = (int)Ef;
-        const float eh = pole ? 0.f : e.hi - (float)F32Scale::SCALE_BITS * Ef;
-        f2 ep = fast_two_sum(eh, pole ? 0.f : e.lo);
-        const float n = floorf(ep.hi);
-        const float fr = (ep.hi - n) + ep.lo;
-        mant = pole ? 0.f : ldexpf(exp2f(fr), (int)n);
-        if (m & 1) mant = -mant;
+        const float lh = (float)ls;
+        seed_f32(m, lh, (float)(ls - (double)lh), lch, lcl, mant, E);
     }
     __device__ static __forceinline__ void phase(int m, uint64_t turn, float& cs, float& sn) {
-        const uint32_t t = (uint32_t)m * (uint32_t)(turn >> 32) + __umulhi((uint32_t)m, (uint32_t)turn);
-        sincospif((float)(int32_t)t * 0x1p-31f, &sn, &cs);
+        phase_f32(m, (uint32_t)(turn >> 32), (uint32_t)turn, cs, sn);
     }
     __device__ static __forceinline__ float down(float v) { return v * 0x1p-64f; }
     __device__ static __forceinline__ float thresh() { return 0x1p-61f; }

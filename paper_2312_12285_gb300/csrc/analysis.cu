@@ -41,12 +41,6 @@ namespace psht {
 // FP32 layout (6 arrays of 4 bytes, stride ntot):
 //   0 x, 1 coeff*w, 2 log2 sin(theta) hi, 3 lo, 4 turn[63:32], 5 turn[31:0]
 // FP64 layout (4 arrays of 8 bytes): 0 x, 1 coeff*w, 2 log2 sin(theta), 3 turn
-__device__ __forceinline__ uint64_t phi_to_turn(double ph) {
-    double t = ph * (1.0 / (2.0 * CUDART_PI));
-    t -= floor(t);
-    if (!(t >= 0.0 && t < 1.0)) t = 0.0;
-    return __double2ull_rn(t * 18446744073709551616.0);
-}
 
 template <typename T>
 __device__ __forceinline__ void prep_one(const PrepParams& p, int64_t j, T x, T ph, T w, double coeff) {
@@ -113,11 +107,6 @@ __global__ void prep_kernel(const __grid_constant__ PrepParams p) {
 //   scan:    per field, bucket-major exclusive offsets over (bucket, CTA range)
 //   scatter: each range, in index order, writes its prepared points to
 //            offset(bucket, range) + rank, ranks taken warp by warp in order.
-__device__ __forceinline__ int x_bucket(double x) {
-    const double a = fabs(x);
-    int b = (int)(a * SORT_BUCKETS);
-    return b < 0 ? 0 : (b >= SORT_BUCKETS ? SORT_BUCKETS - 1 : b);
-}
 
 template <typename T>
 __device__ __forceinline__ bool range_of(const SortParams& sp, int r, int& c, int64_t& i0, int64_t& i1) {
@@ -229,32 +218,11 @@ struct TraitsF32 {
         const float* tf = reinterpret_cast<const float*>(tile);
         x = tf[i];
         w = tf[P + i];
-        const float lh = tf[2 * P + i], ll = tf[3 * P + i];
-        const float mf = (float)m;
-        // e = log2 c_m + m (lh + ll), carried as a float pair
-        const float pr = mf * lh;
-        float pe = fmaf(mf, lh, -pr);
-        pe = fmaf(mf, ll, pe);
-        f2 s = two_sum(pr, lch);
-        f2 e = fast_two_sum(s.hi, s.lo + pe + lcl);
-        // A point at a pole (sin theta = 0, log2 stored as -1e30) has
-        // lambda_mm = 0 for m > 0: it is marked dead for good (E at the floor,
-        // zero mantissa).  Every other point has |e| < 5e4.
-        const bool pole = e.hi < -1.0e7f;
-        const float Ef = pole ? -1048576.f : fminf(0.f, ceilf((e.hi - (float)CE) * (1.0f / SB)));
-        E = (int)Ef;
-        const float eh = pole ? 0.f : e.hi - (float)SB * Ef;
-        f2 ep = fast_two_sum(eh, pole ? 0.f : e.lo);
-        const float n = floorf(ep.hi);
-        const float fr = (ep.hi - n) + ep.lo;
-        mant = pole ? 0.f : ldexpf(exp2f(fr), (int)n);
-        if (m & 1) mant = -mant;
+        seed_f32(m, tf[2 * P + i], tf[3 * P + i], lch, lcl, mant, E);
         phase(tile, P, i, m, cs, sn);
     }
     __device__ static __forceinline__ void phase(const uint32_t* tile, int P, int i, int m, float& cs, float& sn) {
-        const uint32_t t = (uint32_t)m * tile[4 * P + i] + __umulhi((uint32_t)m, tile[5 * P + i]);
-        const float y = (float)(int32_t)t * 0x1p-31f;  // turns * 2 in [-1, 1)
-        sincospif(y, &sn, &cs);
+        phase_f32(m, tile[4 * P + i], tile[5 * P + i], cs, sn);
     }
     __device__ static __forceinline__ float weight(const uint32_t* tile, int P, int i) {
         return reinterpret_cast<const float*>(tile)[P + i];
@@ -1290,30 +1258,21 @@ cudaError_t launch_prep_sorted(const SortParams& sp, cudaStream_t st) {
 template cudaError_t launch_prep_sorted<float>(const SortParams&, cudaStream_t);
 template cudaError_t launch_prep_sorted<double>(const SortParams&, cudaStream_t);
 
-// Occupancy of a kernel at a dynamic shared-memory size, with the attribute
-// raised once per (device, kernel, size).  Cached so that calls made while a
-// stream is being captured into a CUDA graph only enqueue kernels.
+// Bucket offsets only (hist + scan), for callers that scatter the points
+// into a layout of their own.  nranges = sp.range0[ncat].
+cudaError_t launch_sort_offsets_f32(const SortParams& sp, cudaStream_t st) {
+    const int64_t nr = sp.range0[sp.prep.ncat];
+    if (nr == 0) return cudaSuccess;
+    sort_hist_kernel<float><<<(unsigned)nr, 256, 0, st>>>(sp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sort_scan_kernel<<<sp.prep.nfield, SORT_BUCKETS, 0, st>>>(sp);
+    return cudaGetLastError();
+}
+
 template <typename KernelT>
 cudaError_t configure_once(KernelT kern, int threads, size_t smem, int* occ_out) {
-    static std::mutex mu;
-    static std::map<std::pair<int, size_t>, int> cache;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find({dev, smem});
-    if (it != cache.end()) {
-        *occ_out = it->second;
-        return cudaSuccess;
-    }
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    cache[{dev, smem}] = occ;
-    *occ_out = occ;
-    return cudaSuccess;
+    return configure_kernel(reinterpret_cast<const void*>(kern), threads, smem, occ_out);
 }
 
 template <typename Tr, int K, int W>

@@ -35,6 +35,13 @@ cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const
                               cudaStream_t);
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
+cudaError_t launch_sort_offsets_f32(const SortParams&, cudaStream_t);
+size_t mixed_smem_bytes(int);
+int mixed_tile_points();
+int mixed_max_columns();
+int mixed_geometry_arrays();
+cudaError_t launch_mixed_prep(const PrepColsParams&, int64_t, cudaStream_t);
+cudaError_t launch_mixed(const MixedParams&, int, cudaStream_t);
 }  // namespace psht
 
 using namespace psht;
@@ -168,7 +175,8 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
         ll[m] = (float)(l2c[m] - (double)lh[m]);
     }
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    std::vector<float2> af2(af.size());
+    // 32 zero entries past the last column: kernels read whole 32-step blocks
+    std::vector<float2> af2(af.size() + 32, make_float2(0.f, 0.f));
     for (size_t i = 0; i < af.size(); ++i) af2[i] = make_float2(af[i], af[i]);
     const size_t s_af2 = up(af2.size() * 8);
     const size_t s_af = up(af.size() * 4), s_ad = up(ad.size() * 8), s_cs = up(colstart.size() * 8),
@@ -445,7 +453,8 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
     pointsht_status s = check_common(plan, cats, ncat, nfield, prec, "alm");
     if (s != POINTSHT_OK) return s;
     if (prec == POINTSHT_MIXED)
-        return fail(POINTSHT_EINVAL, "alm: POINTSHT_MIXED is not available in this build");
+        return fail(POINTSHT_EINVAL,
+                    "alm: POINTSHT_MIXED applies to weight columns on one point set: use pointsht_alm_columns");
     if (prec != POINTSHT_FP64 && plan->lmax > F32Scale::MAX_LMAX)
         return fail(POINTSHT_EINVAL, "alm: the FP32 path supports lmax <= %d (plan has %d)", F32Scale::MAX_LMAX,
                     plan->lmax);
@@ -522,6 +531,205 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
     rp.out = alm_out;
     cudaError_t e = launch_reduce(rp, st);
     if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm: reduce launch: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+// ---------------------------------------------------- weight columns --
+// Workspace of the mixed column form.
+struct ColLayout {
+    int64_t ntot = 0, chunk = 0, nunits = 0, nranges = 0;
+    int32_t nchunk = 0, npairs = 0, ncolp = 0;
+    size_t pts_off = 0, colmax_off = 0, hist_off = 0, slots_off = 0, counter_off = 0, total = 0;
+};
+
+static void make_col_layout(pointsht_plan plan, int64_t n, int32_t ncol, ColLayout& c) {
+    const int P = mixed_tile_points();
+    const int L = plan->lmax;
+    c.ntot = (n + P - 1) / P * P;
+    c.npairs = L / 2 + 1;
+    c.ncolp = std::min(ncol, mixed_max_columns());
+    // chunk: the largest power-of-two multiple of the tile (at most 2^22
+    // points) that still gives >= 4 units per SM
+    const int64_t target = (int64_t)4 * plan->sm_count;
+    int64_t chunk = P;
+    while (chunk * 2 <= ((int64_t)1 << 22)) chunk *= 2;
+    while (chunk > P && (c.ntot + chunk - 1) / chunk * c.npairs < target) chunk /= 2;
+    c.chunk = chunk;
+    c.nchunk = (int32_t)((c.ntot + chunk - 1) / chunk);
+    c.nunits = (int64_t)c.nchunk * c.npairs;
+    c.nranges = (n + SORT_RANGE - 1) / SORT_RANGE;
+    size_t b = 0;
+    c.pts_off = b;
+    b += up256((size_t)c.ntot * (mixed_geometry_arrays() + ncol) * 4);
+    c.colmax_off = b;
+    b += up256((size_t)ncol * 4);
+    c.hist_off = b;
+    b += up256((size_t)std::max<int64_t>(c.nranges, 1) * SORT_BUCKETS * 8);
+    c.slots_off = b;
+    b += up256((size_t)c.ncolp * c.nchunk * plan->nmodes * 16);
+    c.counter_off = b;
+    b += 256;
+    c.total = b;
+}
+
+static pointsht_status check_columns(pointsht_plan plan, const float* x, const float* phi, const float* w, int64_t n,
+                                     int32_t ncol, pointsht_precision prec, const char* who) {
+    if (!plan) return fail(POINTSHT_EINVAL, "%s: plan is NULL", who);
+    if (n < 0) return fail(POINTSHT_EINVAL, "%s: n=%lld < 0", who, (long long)n);
+    if (ncol < 1 || ncol > PSHT_MAX_FIELDS)
+        return fail(POINTSHT_EINVAL, "%s: ncol=%d outside [1, %d]", who, ncol, PSHT_MAX_FIELDS);
+    if (prec != POINTSHT_FP32 && prec != POINTSHT_MIXED)
+        return fail(POINTSHT_EINVAL, "%s: precision must be POINTSHT_FP32 or POINTSHT_MIXED", who);
+    if (n > 0 && (!x || !phi || !w)) return fail(POINTSHT_EINVAL, "%s: x, phi or w is NULL", who);
+    if (((uintptr_t)x | (uintptr_t)phi | (uintptr_t)w) % 4)
+        return fail(POINTSHT_EINVAL, "%s: x, phi, w are not 4-byte aligned", who);
+    if (plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "%s: the FP32 recurrence supports lmax <= %d (plan has %d)", who,
+                    F32Scale::MAX_LMAX, plan->lmax);
+    if (prec == POINTSHT_MIXED) {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device) != cudaSuccess)
+            return fail(POINTSHT_ECUDA, "%s: cannot query shared memory per block", who);
+        if (mixed_smem_bytes(plan->lmax) > (size_t)optin)
+            return fail(POINTSHT_EINVAL, "%s: lmax=%d needs %zu bytes of shared memory per CTA in the mixed path (%d available)",
+                        who, plan->lmax, mixed_smem_bytes(plan->lmax), optin);
+    }
+    return POINTSHT_OK;
+}
+
+// the FP32 form of the columns: one catalog (and field) per column
+static int32_t column_catalogs(const float* x, const float* phi, const float* w, int64_t n, int32_t ncol,
+                               std::vector<pointsht_catalog>& cats) {
+    cats.assign(ncol, pointsht_catalog{});
+    for (int c = 0; c < ncol; ++c) {
+        cats[c].x = x;
+        cats[c].phi = phi;
+        cats[c].w = w ? w + (size_t)c * n : nullptr;
+        cats[c].n = n;
+        cats[c].field = c;
+        cats[c].coeff = 1.0;
+    }
+    return ncol;
+}
+
+extern "C" size_t pointsht_workspace_size_columns(pointsht_plan plan, int64_t n, int32_t ncol,
+                                                  pointsht_precision prec) {
+    if (!plan || n < 0 || ncol < 1 || ncol > PSHT_MAX_FIELDS || (prec != POINTSHT_FP32 && prec != POINTSHT_MIXED)) {
+        fail(POINTSHT_EINVAL, "workspace_size_columns: bad plan, n, ncol or precision");
+        return 0;
+    }
+    if (prec == POINTSHT_FP32) {
+        std::vector<pointsht_catalog> cats;
+        const float dummy = 0.f;
+        column_catalogs(&dummy, &dummy, &dummy, n, ncol, cats);
+        return pointsht_workspace_size(plan, cats.data(), ncol, ncol, prec);
+    }
+    ColLayout c;
+    make_col_layout(plan, n, ncol, c);
+    return c.total;
+}
+
+extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const float* phi, const float* w,
+                                                int64_t n, int32_t ncol, pointsht_precision prec, double* alm_out,
+                                                void* workspace, size_t ws_bytes, void* stream) {
+    pointsht_status s = check_columns(plan, x, phi, w, n, ncol, prec, "alm_columns");
+    if (s != POINTSHT_OK) return s;
+    if (prec == POINTSHT_FP32) {
+        std::vector<pointsht_catalog> cats;
+        column_catalogs(x, phi, w, n, ncol, cats);
+        return pointsht_alm(plan, cats.data(), ncol, ncol, prec, alm_out, workspace, ws_bytes, stream);
+    }
+    if (!alm_out || ((uintptr_t)alm_out % 16))
+        return fail(POINTSHT_EINVAL, "alm_columns: alm_out NULL or not 16-byte aligned");
+    if ((s = check_device(plan, "alm_columns")) != POINTSHT_OK) return s;
+    ColLayout c;
+    make_col_layout(plan, n, ncol, c);
+    if (!workspace && c.total > 0) return fail(POINTSHT_EINVAL, "alm_columns: workspace is NULL");
+    if ((uintptr_t)workspace % 256) return fail(POINTSHT_EINVAL, "alm_columns: workspace is not 256-byte aligned");
+    if (ws_bytes < c.total)
+        return fail(POINTSHT_ENOMEM, "alm_columns: workspace has %zu bytes, %zu needed", ws_bytes, c.total);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    uint32_t* pts = reinterpret_cast<uint32_t*>(ws + c.pts_off);
+    unsigned* colmax = reinterpret_cast<unsigned*>(ws + c.colmax_off);
+    CUDA_TRY(cudaMemsetAsync(colmax, 0, (size_t)ncol * 4, st));
+    PrepColsParams pp;
+    memset(&pp, 0, sizeof(pp));
+    pp.x = x;
+    pp.phi = phi;
+    pp.w = w;
+    pp.n = n;
+    pp.ncol = ncol;
+    pp.ntot = c.ntot;
+    pp.pts = pts;
+    pp.hist = reinterpret_cast<const int64_t*>(ws + c.hist_off);
+    pp.colmax = colmax;
+    pp.err = plan->err;
+    if (n > 0) {
+        SortParams sp;
+        memset(&sp, 0, sizeof(sp));
+        sp.prep.ncat = 1;
+        sp.prep.nfield = 1;
+        sp.prep.cat[0].x = x;
+        sp.prep.cat[0].phi = phi;
+        sp.prep.cat[0].w = w;
+        sp.prep.cat[0].n = n;
+        sp.prep.cat[0].coeff = 1.0;
+        sp.range0[0] = 0;
+        sp.range0[1] = c.nranges;
+        sp.field_off[0] = 0;
+        sp.hist = reinterpret_cast<int64_t*>(ws + c.hist_off);
+        cudaError_t e = launch_sort_offsets_f32(sp, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: sort launch: %s", cudaGetErrorString(e));
+    }
+    if (c.ntot > 0) {
+        cudaError_t e = launch_mixed_prep(pp, c.nranges, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: prep launch: %s", cudaGetErrorString(e));
+    }
+    for (int col0 = 0; col0 < ncol; col0 += c.ncolp) {
+        const int nc = std::min(c.ncolp, ncol - col0);
+        if (c.nunits > 0) {
+            CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
+            MixedParams mp;
+            memset(&mp, 0, sizeof(mp));
+            mp.lmax = plan->lmax;
+            mp.ncol = nc;
+            mp.npairs = c.npairs;
+            mp.flush_tiles = FLUSH_TILES;
+            mp.nmodes = plan->nmodes;
+            mp.chunk = c.chunk;
+            mp.nunits = c.nunits;
+            mp.ntot = c.ntot;
+            mp.nchunk = c.nchunk;
+            mp.pts = pts;
+            mp.wcols = pts + (size_t)(mixed_geometry_arrays() + col0) * c.ntot;
+            mp.colmax = colmax + col0;
+            mp.alpha2 = plan->alpha_f2;
+            mp.colstart = plan->colstart;
+            mp.log2c_hi = plan->log2c_hi;
+            mp.log2c_lo = plan->log2c_lo;
+            mp.slots = reinterpret_cast<double*>(ws + c.slots_off);
+            mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
+            mp.err = plan->err;
+            if (plan->ev_start && col0 == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
+            cudaError_t e = launch_mixed(mp, plan->sm_count, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: mixed launch: %s", cudaGetErrorString(e));
+            if (plan->ev_stop && col0 + nc >= ncol) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
+        }
+        ReduceParams rp;
+        memset(&rp, 0, sizeof(rp));
+        rp.nfield = nc;
+        rp.nmodes = plan->nmodes;
+        for (int f = 0; f < nc; ++f) {
+            rp.slot0[f] = f * c.nchunk;
+            rp.nchunk[f] = c.nunits > 0 ? c.nchunk : 0;
+        }
+        rp.slots = reinterpret_cast<const double*>(ws + c.slots_off);
+        rp.gamma = plan->gamma;
+        rp.out = alm_out + (size_t)col0 * plan->nmodes * 2;
+        cudaError_t e = launch_reduce(rp, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: reduce launch: %s", cudaGetErrorString(e));
+    }
     return POINTSHT_OK;
 }
 

@@ -15,12 +15,54 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+#include <utility>
+
 #define PSHT_MAX_FIELDS 64
 #define PSHT_MAX_CATS 128
 
 namespace psht {
 
 enum ErrBits : unsigned { ERR_RANGE = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+
+// Launch configuration of a kernel with dynamic shared memory.  The
+// function's maximum dynamic shared memory is raised once per (device,
+// kernel) to the device's opt-in limit, so that no later launch of a smaller
+// size can lower it below a size already in use; occupancy is cached per
+// (device, kernel, size).  After the first call for a size, no runtime call is
+// made, so launches made while a stream is being captured into a CUDA graph
+// only enqueue kernels.
+inline cudaError_t configure_kernel(const void* kern, int threads, size_t smem, int* occ_out) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> raised;
+    static std::map<std::tuple<int, const void*, size_t>, int> occ_cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = occ_cache.find(std::make_tuple(dev, kern, smem));
+    if (it != occ_cache.end()) {
+        *occ_out = it->second;
+        return cudaSuccess;
+    }
+    if (!raised.count({dev, kern})) {
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return e;
+        raised.insert({dev, kern});
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    occ_cache[std::make_tuple(dev, kern, smem)] = occ;
+    *occ_out = occ;
+    return cudaSuccess;
+}
 
 // Rescaling of the recurrence state below the floating-point range (the
 // paper does not discuss underflow; Pbar_m^m ~ sin^m(theta) leaves the FP32
@@ -98,6 +140,23 @@ struct PrepParams {
 #define SORT_BUCKETS 256
 #define SORT_RANGE 4096  // points per CTA range of the counting sort
 
+#ifdef __CUDACC__
+// |x| bucket of the counting sort (points ordered by |x|, see analysis.cu)
+__device__ __forceinline__ int x_bucket(double x) {
+    const double a = fabs(x);
+    int b = (int)(a * SORT_BUCKETS);
+    return b < 0 ? 0 : (b >= SORT_BUCKETS ? SORT_BUCKETS - 1 : b);
+}
+
+// phi (radians, any finite value) as a 64-bit fixed-point fraction of a turn
+__device__ __forceinline__ uint64_t phi_to_turn(double ph) {
+    double t = ph * (1.0 / (2.0 * 3.14159265358979323846));
+    t -= floor(t);
+    if (!(t >= 0.0 && t < 1.0)) t = 0.0;
+    return __double2ull_rn(t * 18446744073709551616.0);
+}
+#endif
+
 struct SortParams {
     PrepParams prep;                     // catalogs (dst unused), pads, output
     int64_t range0[PSHT_MAX_CATS + 1];   // first CTA range of each catalog
@@ -113,6 +172,38 @@ struct ReduceParams {
     const double* slots;
     const double* gamma;
     double* out;
+};
+
+// Weight-column form (mixed.cu).  Layout written by its preparation: five
+// geometry arrays (x, log2 sin theta hi, lo, turn hi, turn lo) and then ncol
+// weight arrays, each of ntot 4-byte values, points in |x| order.
+struct PrepColsParams {
+    const float* x;
+    const float* phi;
+    const float* w;        // [ncol][n]
+    int64_t n;
+    int32_t ncol, pad_;
+    int64_t ntot;          // padded points (multiple of the tile)
+    uint32_t* pts;         // (5 + ncol) arrays of ntot
+    const int64_t* hist;   // sorted offsets per (range, bucket)
+    unsigned* colmax;      // [ncol] bits of max |w| (non-negative floats order as integers)
+    unsigned* err;
+};
+
+struct MixedParams {
+    int32_t lmax, ncol, npairs, flush_tiles;
+    int64_t nmodes, chunk, nunits, ntot;
+    int32_t nchunk, pad_;
+    const uint32_t* pts;      // geometry arrays (5 x ntot)
+    const uint32_t* wcols;    // this pass's first weight array (ncol x ntot)
+    const unsigned* colmax;   // this pass's columns
+    const float2* alpha2;
+    const int64_t* colstart;
+    const float* log2c_hi;
+    const float* log2c_lo;
+    double* slots;            // [col][chunk][nmodes] complex
+    int* counter;
+    unsigned* err;
 };
 
 struct AdjointParams {
@@ -197,6 +288,38 @@ __device__ __forceinline__ f2 two_sum(float a, float b) {
 __device__ __forceinline__ f2 fast_two_sum(float a, float b) {
     float s = a + b;
     return {s, b - (s - a)};
+}
+
+// ------------------------------------------ FP32 seed and phase (App. A) --
+// lambda_mm = mant * 2^(64 E): log2 |lambda_mm| = log2 c_m + m log2 sin(theta)
+// carried as a float pair (lh + ll for log2 sin theta, lch + lcl for
+// log2 c_m), split into an exponent block E <= 0 and a mantissa in
+// [2^-125, 2^-61] (E < 0) or (2^-125, ~1] (E = 0).  A point at a pole
+// (log2 sin theta stored as -1e30) gets E at the floor and mantissa 0.
+__device__ __forceinline__ void seed_f32(int m, float lh, float ll, float lch, float lcl, float& mant, int& E) {
+    const float mf = (float)m;
+    const float pr = mf * lh;
+    float pe = fmaf(mf, lh, -pr);
+    pe = fmaf(mf, ll, pe);
+    const f2 s = two_sum(pr, lch);
+    const f2 e = fast_two_sum(s.hi, s.lo + pe + lcl);
+    const bool pole = e.hi < -1.0e7f;
+    const float Ef =
+        pole ? -1048576.f : fminf(0.f, ceilf((e.hi - (float)F32Scale::CHECK_EXP) * (1.0f / F32Scale::SCALE_BITS)));
+    E = (int)Ef;
+    const float eh = pole ? 0.f : e.hi - (float)F32Scale::SCALE_BITS * Ef;
+    const f2 ep = fast_two_sum(eh, pole ? 0.f : e.lo);
+    const float n = floorf(ep.hi);
+    const float fr = (ep.hi - n) + ep.lo;
+    mant = pole ? 0.f : ldexpf(exp2f(fr), (int)n);
+    if (m & 1) mant = -mant;
+}
+
+// e^{i m phi} from phi as a 64-bit fixed-point turn (hi, lo words):
+// (m * turn) mod 2^64, top 32 bits as a signed fraction of a half turn.
+__device__ __forceinline__ void phase_f32(int m, uint32_t thi, uint32_t tlo, float& cs, float& sn) {
+    const uint32_t t = (uint32_t)m * thi + __umulhi((uint32_t)m, tlo);
+    sincospif((float)(int32_t)t * 0x1p-31f, &sn, &cs);
 }
 #endif
 

@@ -1,0 +1,478 @@
+// mixed.cu -- per-m contraction on tensor cores for several weight columns
+// sharing one point set (POINTSHT_MIXED).
+//
+// For order m the transform of F weight columns is the contraction over points
+//   a_m[l, f] = sum_i lambda_lm(x_i) W_m[i, f],  W_m[i, f] = w_f,i e^{-i m phi_i}
+// (Eq. alm_def for each column).  lambda comes from the same FP32 sign-folded
+// recurrence as the FP32 kernel (App. A); the contraction runs on the tensor
+// cores in fp16 with a hi + lo split of both operands and FP32 accumulation:
+//   a = W_hi lambda_hi + W_lo lambda_hi + W_hi lambda_lo   (lo x lo dropped,
+// about 2^-22 of each product).
+//
+// Shape of one warp-level mma.sync.m16n8k16 (fp16 in, fp32 accumulate):
+//   A (16 x 16) = W^T of one 16-point group: rows 0..7 = (field f, re/im) of
+//                 W_hi (f = row/2), rows 8..15 = the same of W_lo; kept in
+//                 registers for the whole column (W does not depend on l);
+//   B (16 x 8)  = lambda of those 16 points at 8 consecutive l, staged as fp16
+//                 hi and lo rows in shared memory and read with ldmatrix.trans;
+//   D (16 x 8)  = sums over the warp's points; rows r and r + 8 are added.
+// Only 8 l are staged at a time (4 KB per warp): the recurrence hands its
+// values to the tensor cores every 8 steps.
+//
+// CTA: 8 warps on one order pair (m, lmax - m), tiles of 1024 points (128 per
+// warp, 4 per lane as two f32x2 pairs).  Every 32 steps the warps' partial
+// sums meet in shared memory and are added, in warp order, to the CTA's FP32
+// accumulator rows (deterministic); rows are flushed to FP64 slots per chunk.
+// Rounds of 8 steps are software-pipelined: the recurrence of round r runs
+// while the MMAs of round r - 1 are in flight.  Points still below the FP32
+// range contribute nothing: their hi part is masked to zero and their lo part
+// multiplied by zero in the split itself, and a warp whose points are all
+// below range skips the split and the MMAs (its partial sums are exact zeros).
+//
+// Each weight column is scaled by a power of two (exact) so that its largest
+// |w| lies in [1, 2): fp16 then holds every W without overflow, and the scale
+// is undone in FP64 when the rows are flushed.
+#include "common.cuh"
+
+#include <cuda_fp16.h>
+
+namespace psht {
+
+constexpr int MX_WARPS = 8;
+constexpr int MX_KQ = 4;                       // points per lane
+constexpr int MX_PW = 32 * MX_KQ;              // points per warp (128)
+constexpr int MX_P = MX_WARPS * MX_PW;         // points per tile (1024)
+constexpr int MX_MAXCOL = 4;                   // weight columns per pass
+constexpr int MX_NGEO = 5;                     // x, lsh, lsl, turn hi, turn lo
+constexpr int MX_BLK = 32;                     // steps between CTA combines
+
+// ---------------------------------------------------------------- prep --
+__device__ __forceinline__ void mx_write(const PrepColsParams& p, int64_t j, float x, float ph, int64_t src) {
+    bool ok = isfinite(x) && isfinite(ph) && fabsf(x) <= 1.f;
+    for (int f = 0; f < p.ncol && src >= 0; ++f) ok &= isfinite(p.w[(int64_t)f * p.n + src]);
+    if (!ok) {
+        atomicOr(p.err, ERR_RANGE);
+        x = 0.f;
+        ph = 0.f;
+    }
+    const double xd = (double)x;
+    const double s2 = (1.0 - xd) * (1.0 + xd);
+    const double ls = s2 > 0.0 ? 0.5 * log2(s2) : -1.0e30;
+    const uint64_t turn = phi_to_turn((double)ph);
+    float* b = reinterpret_cast<float*>(p.pts);
+    const float lh = (float)ls;
+    b[j] = x;
+    b[p.ntot + j] = lh;
+    b[2 * p.ntot + j] = (float)(ls - (double)lh);
+    p.pts[3 * p.ntot + j] = (uint32_t)(turn >> 32);
+    p.pts[4 * p.ntot + j] = (uint32_t)(turn & 0xffffffffu);
+    for (int f = 0; f < p.ncol; ++f)
+        b[(MX_NGEO + f) * p.ntot + j] = (ok && src >= 0) ? p.w[(int64_t)f * p.n + src] : 0.f;
+}
+
+// stable counting-sort scatter of the points into |x| order (offsets from
+// the histogram / scan kernels of analysis.cu), plus the column maxima
+__global__ void __launch_bounds__(256) mx_scatter_kernel(const __grid_constant__ PrepColsParams p) {
+    __shared__ int64_t next[SORT_BUCKETS];
+    __shared__ int wcnt[8][SORT_BUCKETS];
+    const int r = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) next[b] = p.hist[(int64_t)r * SORT_BUCKETS + b];
+    const int64_t i0 = (int64_t)r * SORT_RANGE, i1 = min(p.n, i0 + SORT_RANGE);
+    __syncthreads();
+    for (int64_t base = i0; base < i1; base += 256) {
+        for (int b = lane; b < SORT_BUCKETS; b += 32) wcnt[warp][b] = 0;
+        __syncwarp();
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < i1;
+        const float x = valid ? p.x[i] : 0.f;
+        const int bk = valid ? x_bucket((double)x) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp][bk] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int64_t dst = next[bk] + rank;
+            for (int w = 0; w < warp; ++w) dst += wcnt[w][bk];
+            mx_write(p, dst, x, p.phi[i], i);
+        }
+        for (int f = 0; f < p.ncol; ++f) {
+            const float v = valid ? fabsf(p.w[(int64_t)f * p.n + i]) : 0.f;
+            const unsigned bits = isfinite(v) ? __float_as_uint(v) : 0u;
+            const unsigned mx = __reduce_max_sync(0xffffffffu, bits);
+            if (lane == 0 && mx) atomicMax(&p.colmax[f], mx);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += wcnt[w][b];
+            next[b] += s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void mx_pad_kernel(const __grid_constant__ PrepColsParams p) {
+    for (int64_t j = p.n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < p.ntot;
+         j += (int64_t)gridDim.x * blockDim.x)
+        mx_write(p, j, 0.f, 0.f, -1);
+}
+
+// ------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ float2 mx_fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)),
+          "l"(reinterpret_cast<unsigned long long&>(c)));
+    return d;
+}
+__device__ __forceinline__ float2 mx_mul2(float2 a, float2 b) {
+    float2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
+// two f32 -> packed f16x2 with `a` in the low half, saturating to the finite range
+__device__ __forceinline__ uint32_t mx_pack(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+__device__ __forceinline__ void mx_ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void mx_mma(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                       uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// exponent e with max|w| * 2^-e in [1, 2) (0 for an all-zero column)
+__device__ __forceinline__ int mx_col_exp(unsigned bits) {
+    if (bits == 0u) return 0;
+    const int e = ilogbf(__uint_as_float(bits));
+    return e < -120 ? -120 : (e > 120 ? 120 : e);
+}
+
+// ------------------------------------------------------------ kernel --
+__global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const __grid_constant__ MixedParams p) {
+    constexpr int ARR = MX_P * 4;  // bytes of one array in a tile
+    const int narr = MX_NGEO + p.ncol;
+    const int TILE = narr * ARR;
+    const int L = p.lmax;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    int64_t* s_unit = reinterpret_cast<int64_t*>(smem + 16);
+    unsigned char* tiles = smem + 128;
+    uint4* stage = reinterpret_cast<uint4*>(tiles + 2 * (MX_NGEO + MX_MAXCOL) * ARR);  // [warp][plane][128]
+    float2* phs = reinterpret_cast<float2*>(stage + MX_WARPS * 2 * MX_PW);               // [warp][128]
+    float* part = reinterpret_cast<float*>(phs + MX_WARPS * MX_PW);                      // [2][warp][32][8]
+    float* acc = part + 2 * MX_WARPS * MX_BLK * 8;                                       // [(L+2)][8]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, c4 = lane & 3;
+    const int qbase = warp * MX_PW;
+    uint4* my_stage = stage + warp * 2 * MX_PW;
+    float2* my_ph = phs + warp * MX_PW;
+    const uint32_t stage_addr = smem_u32(my_stage);
+    const uint32_t ld_addr = stage_addr + (uint32_t)(((lane >> 4) * MX_PW + (lane & 15)) * 16);
+
+    // this lane's A rows are field g >> 1: its column scale
+    const int myf = g >> 1;
+    const float wscale = myf < p.ncol ? ldexpf(1.f, -mx_col_exp(p.colmax[myf])) : 0.f;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity0 = 0, parity1 = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_unit[0] = (int64_t)atomicAdd(p.counter, 1);
+        __syncthreads();
+        const int64_t u = s_unit[0];
+        __syncthreads();
+        if (u >= p.nunits) break;
+        const int64_t r = u / p.npairs;
+        const int pi = (int)(u - r * p.npairs);
+        const int64_t pt0 = r * p.chunk;
+        const int64_t npts = min(p.chunk, p.ntot - pt0);
+        const int ntiles = (int)(npts / MX_P);
+        const int ma = pi, mb = L - pi;
+        const bool single = ma == mb;
+        const int lena = L - ma + 1, lenb = single ? 0 : L - mb + 1;
+        for (int i = threadIdx.x; i < (lena + lenb) * 8; i += blockDim.x) acc[i] = 0.f;
+        bool first_flush = true;
+        __syncthreads();
+
+        auto issue = [&](int t, int b) {
+            uint64_t* bar = &bars[b];
+            unsigned char* dst = tiles + b * TILE;
+            mbar_expect_tx(bar, narr * ARR);
+            const int64_t first = pt0 + (int64_t)t * MX_P;
+            for (int a = 0; a < MX_NGEO; ++a) bulk_g2s(dst + a * ARR, p.pts + (int64_t)a * p.ntot + first, ARR, bar);
+            for (int f = 0; f < p.ncol; ++f)
+                bulk_g2s(dst + (MX_NGEO + f) * ARR, p.wcols + (int64_t)f * p.ntot + first, ARR, bar);
+        };
+        if (threadIdx.x == 0 && ntiles > 0) issue(0, 0);
+
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            if (threadIdx.x == 0 && t + 1 < ntiles) issue(t + 1, b ^ 1);
+            const uint32_t par = b ? parity1 : parity0;
+            const bool ok = mbar_wait_bounded(&bars[b], par);
+            if (b) parity1 ^= 1u;
+            else parity0 ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(p.err, ERR_TIMEOUT);
+                    if (t + 1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], b ? parity0 : parity1);
+                }
+                return;
+            }
+            const float* tf = reinterpret_cast<const float*>(tiles + b * TILE);
+            const uint32_t* tu = reinterpret_cast<const uint32_t*>(tf);
+
+            for (int col = 0; col < (single ? 1 : 2); ++col) {
+                const int m = col ? mb : ma;
+                const int len = L - m + 1;
+                float* cacc = acc + (col ? lena : 0) * 8;
+                const float2* alpha2 = p.alpha2 + p.colstart[m];
+                const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
+                // ---- per-point seed, phase and state (4 points per lane) ----
+                float2 x2[2], p1[2], p2[2], alive[2];
+                uint32_t mask[4];
+                int E[4];
+#pragma unroll
+                for (int k = 0; k < MX_KQ; ++k) {
+                    const int q = 32 * k + lane, i = qbase + q;
+                    float mant, cs, sn;
+                    seed_f32(m, tf[MX_P + i], tf[2 * MX_P + i], lch, lcl, mant, E[k]);
+                    phase_f32(m, tu[3 * MX_P + i], tu[4 * MX_P + i], cs, sn);
+                    my_ph[q] = make_float2(cs, sn);
+                    const float xv = tf[i];
+                    const float al = E[k] == 0 ? 1.f : 0.f;
+                    if (k & 1) {
+                        x2[k >> 1].y = xv;
+                        p2[k >> 1].y = mant;
+                        p1[k >> 1].y = 0.f;
+                        alive[k >> 1].y = al;
+                    } else {
+                        x2[k >> 1].x = xv;
+                        p2[k >> 1].x = mant;
+                        p1[k >> 1].x = 0.f;
+                        alive[k >> 1].x = al;
+                    }
+                    mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
+                }
+                __syncwarp();
+                // ---- A fragments: W^T hi (rows 0..7) and lo (rows 8..15) per 16-point group ----
+                uint32_t A[8][4];
+                {
+                    const int comp = g & 1;
+#pragma unroll
+                    for (int gi = 0; gi < 8; ++gi) {
+                        float hv[4], lv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
+                            float wv = 0.f;
+                            if (myf < p.ncol) {
+                                const float2 ph = my_ph[q];
+                                const float w = tf[(MX_NGEO + myf) * MX_P + qbase + q] * wscale;
+                                wv = comp ? -w * ph.y : w * ph.x;
+                            }
+                            hv[e] = __half2float(__float2half_rn(wv));
+                            lv[e] = wv - hv[e];
+                        }
+                        A[gi][0] = mx_pack(hv[0], hv[1]);
+                        A[gi][1] = mx_pack(lv[0], lv[1]);
+                        A[gi][2] = mx_pack(hv[2], hv[3]);
+                        A[gi][3] = mx_pack(lv[2], lv[3]);
+                    }
+                }
+                bool lane_neg = (E[0] | E[1] | E[2] | E[3]) != 0;
+                bool any_neg = __any_sync(0xffffffffu, lane_neg);
+                // a warp all of whose points are still below the FP32 range
+                // contributes exact zeros: it runs the recurrence only
+                bool warp_alive = __any_sync(0xffffffffu, (E[0] == 0) | (E[1] == 0) | (E[2] == 0) | (E[3] == 0));
+                const int nrounds = 4 * ((len + MX_BLK - 1) / MX_BLK);
+                // Software pipeline over rounds of 8 steps: round r's
+                // recurrence and split run while round r-1's MMAs are in
+                // flight; round r-1's sums are stored after that.
+                float Da[4], Db[4], Dc[4], Dd[4];
+                bool act_prev = false;
+                for (int r = 0; r <= nrounds; ++r) {
+                    const bool have = r < nrounds;
+                    const bool act = have && warp_alive;
+                    uint32_t hi[4][4], lo[4][4];
+                    if (have) {
+                        const float4* a4 = reinterpret_cast<const float4*>(alpha2 + 8 * r);
+#pragma unroll
+                        for (int j2 = 0; j2 < 4; ++j2) {
+                            const float4 av4 = __ldg(a4 + j2);
+                            const float2 av[2] = {make_float2(av4.x, av4.y), make_float2(av4.z, av4.w)};
+                            float2 s0[2];
+#pragma unroll
+                            for (int jj = 0; jj < 2; ++jj) {
+#pragma unroll
+                                for (int kp = 0; kp < 2; ++kp) {
+                                    const float2 sg = mx_fma2(av[jj], mx_mul2(x2[kp], p1[kp]), p2[kp]);
+                                    p2[kp] = p1[kp];
+                                    p1[kp] = sg;
+                                }
+                                if (jj == 0) {
+                                    s0[0] = p1[0];
+                                    s0[1] = p1[1];
+                                }
+                            }
+                            if (act) {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    const float va = (k & 1) ? s0[k >> 1].y : s0[k >> 1].x;
+                                    const float vb = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
+                                    const float al = (k & 1) ? alive[k >> 1].y : alive[k >> 1].x;
+                                    const float ha = __uint_as_float(__float_as_uint(va) & mask[k]);
+                                    const float hb = __uint_as_float(__float_as_uint(vb) & mask[k]);
+                                    hi[k][j2] = mx_pack(ha, hb);
+                                    lo[k][j2] = mx_pack(fmaf(va, al, -ha), fmaf(vb, al, -hb));
+                                }
+                            }
+                        }
+                        if (any_neg && (r & 1)) {
+                            // rescale check every 16 steps (F32Scale: 2^64 blocks)
+                            lane_neg = false;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
+                                float& bb = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
+                                const bool nd = (E[k] < 0) & (fmaxf(fabsf(a), fabsf(bb)) > 0x1p-61f);
+                                const float sc = nd ? 0x1p-64f : 1.f;
+                                a *= sc;
+                                bb *= sc;
+                                E[k] += nd;
+                                mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
+                                if (k & 1) alive[k >> 1].y = E[k] == 0 ? 1.f : 0.f;
+                                else alive[k >> 1].x = E[k] == 0 ? 1.f : 0.f;
+                                lane_neg |= E[k] != 0;
+                            }
+                            any_neg = __any_sync(0xffffffffu, lane_neg);
+                            warp_alive = __any_sync(0xffffffffu, (E[0] == 0) | (E[1] == 0) | (E[2] == 0) | (E[3] == 0));
+                        }
+                    }
+                    if (r >= 1) {
+                        // round r-1: row g (W_hi terms) + row g + 8 (W_lo terms),
+                        // columns l = 8 (r-1) + 2 c4 (+1) of the column
+                        const int rp = r - 1;
+                        float* pb = part + ((rp >> 2) & 1) * (MX_WARPS * MX_BLK * 8);
+                        const int row = warp * MX_BLK + 8 * (rp & 3) + 2 * c4;
+                        pb[row * 8 + g] = act_prev ? ((Da[0] + Db[0]) + (Dc[0] + Dd[0])) + (Da[2] + Db[2]) : 0.f;
+                        pb[(row + 1) * 8 + g] = act_prev ? ((Da[1] + Db[1]) + (Dc[1] + Dd[1])) + (Da[3] + Db[3]) : 0.f;
+                        if ((r & 3) == 0) {
+                            // block (r-1)/4 complete in every warp: add the
+                            // warps' partial sums in warp order
+                            __syncthreads();
+                            const int bk = (r >> 2) - 1;
+                            const int li = threadIdx.x >> 3, v = threadIdx.x & 7;  // 32 l x 8 values
+                            const int q = MX_BLK * bk + li;
+                            if (q < len) {
+                                const float* pbb = part + (bk & 1) * (MX_WARPS * MX_BLK * 8);
+                                float sacc = cacc[q * 8 + v];
+#pragma unroll
+                                for (int w = 0; w < MX_WARPS; ++w) sacc += pbb[(w * MX_BLK + li) * 8 + v];
+                                cacc[q * 8 + v] = sacc;
+                            }
+                        }
+                    }
+                    if (act) {
+                        __syncwarp();  // every lane has read the previous round's stage
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            my_stage[32 * k + lane] = make_uint4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+                            my_stage[MX_PW + 32 * k + lane] = make_uint4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) Da[e] = Db[e] = Dc[e] = Dd[e] = 0.f;
+#pragma unroll
+                        for (int gi = 0; gi < 8; ++gi) {
+                            uint32_t bh0, bh1, bl0, bl1;
+                            mx_ldsm_x4_t(ld_addr + (uint32_t)(16 * gi * 16), bh0, bh1, bl0, bl1);
+                            if (gi & 1) {
+                                mx_mma(Db, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bh0, bh1);
+                                mx_mma(Dd, A[gi][0], 0u, A[gi][2], 0u, bl0, bl1);
+                            } else {
+                                mx_mma(Da, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bh0, bh1);
+                                mx_mma(Dc, A[gi][0], 0u, A[gi][2], 0u, bl0, bl1);
+                            }
+                        }
+                    }
+                    act_prev = act;
+                }
+                __syncthreads();  // the column's rows are complete; phases may be rewritten
+            }
+            // ---- flush the accumulator rows into this chunk's FP64 slots ----
+            if (t == ntiles - 1 || (t + 1) % p.flush_tiles == 0) {
+                for (int i = threadIdx.x; i < (lena + lenb) * 8; i += blockDim.x) {
+                    const int q = i >> 3, v = i & 7;
+                    const int f = v >> 1;
+                    if (f < p.ncol) {
+                        const int m = q < lena ? ma : mb;
+                        const int l = q < lena ? ma + q : mb + (q - lena);
+                        double* sp =
+                            p.slots + (((int64_t)f * p.nchunk + r) * p.nmodes + tri_base(m, L) + l) * 2 + (v & 1);
+                        const double val = ldexp((double)acc[i], mx_col_exp(p.colmax[f]));
+                        *sp = (first_flush ? 0.0 : *sp) + val;
+                    }
+                    acc[i] = 0.f;
+                }
+                first_flush = false;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers --
+size_t mixed_smem_bytes(int lmax) {
+    const size_t accf = (size_t)(lmax + 2) * 8;
+    return 128 + 2 * (size_t)(MX_NGEO + MX_MAXCOL) * MX_P * 4 + (size_t)MX_WARPS * 2 * MX_PW * 16 +
+           (size_t)MX_WARPS * MX_PW * 8 + (size_t)2 * MX_WARPS * MX_BLK * 8 * 4 + accf * 4;
+}
+
+int mixed_tile_points() { return MX_P; }
+int mixed_max_columns() { return MX_MAXCOL; }
+int mixed_geometry_arrays() { return MX_NGEO; }
+
+cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStream_t st) {
+    mx_pad_kernel<<<64, 256, 0, st>>>(pp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nranges == 0) return e;
+    mx_scatter_kernel<<<(unsigned)nranges, 256, 0, st>>>(pp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
+    const size_t smem = mixed_smem_bytes(mp.lmax);
+    int occ = 0;
+    cudaError_t e = configure_kernel(reinterpret_cast<const void*>(analysis_mixed_kernel), MX_WARPS * 32, smem, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)sm_count * occ;
+    if (grid > mp.nunits) grid = mp.nunits;
+    if (grid < 1) grid = 1;
+    analysis_mixed_kernel<<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    return cudaGetLastError();
+}
+
+}  // namespace psht

@@ -145,6 +145,38 @@ def alm_raw(plan: Plan, cats, nfield: int = 1, precision: str = "fp32", out=None
     return out
 
 
+def workspace_bytes_columns(plan: Plan, n: int, ncol: int, precision: str = "mixed") -> int:
+    size = plan.lib.pointsht_workspace_size_columns(plan.handle, int(n), int(ncol), _lib.PRECISIONS[precision])
+    if size == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_columns")
+    return int(size)
+
+
+def alm_columns(plan: Plan, x: torch.Tensor, phi: torch.Tensor, w: torch.Tensor, precision: str = "mixed", out=None,
+                workspace=None, stream=None):
+    """a_lm of F weight columns on one point set (pointsht_alm_columns).
+
+    x, phi: float32 [n]; w: float32 [F, n] (row f = column f of the ABI);
+    returns complex128 [F, M].  "mixed" runs the per-m contraction on the
+    tensor cores, "fp32" the plain FP32 path with one field per column."""
+    dev = plan.device
+    for name, t in (("x", x), ("phi", phi), ("w", w)):
+        if t.device != dev or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor on {dev}")
+    if w.dim() != 2 or x.dim() != 1 or phi.shape != x.shape or w.shape[1] != x.shape[0]:
+        raise ValueError("expected x, phi of shape [n] and w of shape [F, n]")
+    ncol, n = int(w.shape[0]), int(w.shape[1])
+    need = workspace_bytes_columns(plan, n, ncol, precision)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    if out is None:
+        out = torch.empty((ncol, plan.nmodes), dtype=torch.complex128, device=dev)
+    _lib.check(plan.lib.pointsht_alm_columns(plan.handle, _ptr(x), _ptr(phi), _ptr(w), n, ncol,
+                                             _lib.PRECISIONS[precision], _ptr(out), _ptr(workspace),
+                                             workspace.numel(), _stream_ptr(stream)), "alm_columns")
+    return out
+
+
 def shot_noise_raw(cats, nfield: int, precision: str, device, workspace=None, stream=None, weights=None):
     """Shot-noise matrix [nfield, nfield] (pointsht_shot_noise)."""
     lib = _lib.load()
