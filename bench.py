@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--config", type=int, default=3, help="workload configuration (3 = lmax 2048, 1e7 points)")
     ap.add_argument("--scale", type=float, default=1.0, help="scale the point counts (profiling runs)")
     ap.add_argument("--lmax", type=int, default=None)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--columns", type=int, default=0,
+                    help="weight columns on the workload's point set (pointsht_alm_columns); 0 = catalog form")
+    ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
@@ -116,17 +119,22 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(workload: str, npoints: int):
-    """DRAM bytes per launch of the analysis kernel from a committed ncu summary,
-    scaled to this launch's points; None if absent or the kernel changed since."""
-    path = os.path.join(ROOT, "profiles", "analysis_kernel_traffic.json")
+    """DRAM bytes per launch of the analysis kernel from the committed ncu
+    summary (profiles/analysis_kernel_lognormal_cap_l2048_traffic.md), scaled
+    to this launch's points; None if absent, for another workload, or if the
+    kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "analysis_kernel_lognormal_cap_l2048_traffic.md")
     try:
-        d = json.load(open(path))
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", " ", "#")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_hash") != kernel_source_hash() or workload != "lognormal_cap_l2048":
+            return None
+        return float(kv["dram_bytes_per_launch"]) / float(kv["points"]) * npoints
     except Exception:
         return None
-    if d.get("kernel_hash") != kernel_source_hash():
-        return None
-    per_pt = d.get("dram_bytes_per_launch") / max(1, d.get("points"))
-    return per_pt * npoints
 
 
 def load_workload(args):
@@ -377,6 +385,11 @@ def ours(args):
         accuracy = {"cl_err_vs_fp64_oracle": max(errs), "alm_rel_err_per_l": max(
             oracle.rel_err_per_l(a[f], ref[f], L) for f in range(nfield)),
             "sample_points": npts, "definition": "max over 1<=l<=lmax of |C_l - C_l^ref| / C_l^ref"}
+        ladder_sample = (sample, ref[0]) if nfield == 1 else None
+    ladder = None
+    if rank == 0 and world == 1 and not args.no_ladder and prec == "fp32" and wl.nfield == 1:
+        ladder = precision_ladder(wl, plan, dev, value, accuracy["cl_err_vs_fp64_oracle"] if accuracy else None,
+                                  ladder_sample if accuracy else None)
 
     if rank == 0:
         line = {
@@ -399,6 +412,287 @@ def ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "accuracy": accuracy,
+            "precision_ladder": ladder,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- weight columns --
+def mixed_mma_flops_per_point_mode(F: int) -> float:
+    """Tensor-core flops the mixed kernel issues per point x mode of one pass:
+    per 16 points x 8 multipoles, 2 (4-column kernel) or 3 (8-column kernel)
+    m16n8k16 MMAs of 2 x 16 x 8 x 16 flops."""
+    nmma = 2 if F <= 4 else 3
+    return nmma * 2 * 16 * 8 * 16 / (16 * 8)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def time_columns(plan, xd, pd, Wd, prec, reps, warm=1):
+    """Device time (ms) of pointsht_alm_columns: whole call and kernel(s) alone."""
+    import torch
+
+    from paper_2312_12285_gb300 import ops
+    n, F = int(xd.shape[0]), int(Wd.shape[0])
+    ws = torch.empty(max(256, ops.workspace_bytes_columns(plan, n, F, prec)), dtype=torch.uint8, device=xd.device)
+    out = torch.empty((F, plan.nmodes), dtype=torch.complex128, device=xd.device)
+    for _ in range(warm):
+        ops.alm_columns(plan, xd, pd, Wd, prec, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a_, b_ in evk:
+        a_.record()
+        b_.record()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(reps):
+        plan.set_timing_events(evk[k][0], evk[k][1])
+        ops.alm_columns(plan, xd, pd, Wd, prec, out=out, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.set_timing_events(None, None)
+    plan.check()
+    return e0.elapsed_time(e1) / reps, sum(a.elapsed_time(b) for a, b in evk) / reps, out
+
+
+def precision_ladder(wl, plan, dev, fp32_value, fp32_cl_err, sample):
+    """Mixed path for F = 1, 4, 8 weight columns on the workload's point set
+    (per-column throughput, speed-up over the plain FP32 path at the same F,
+    C_l error against the FP64 oracle on the bench sample), and the FP64 path
+    on a 1% subsample."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2312_12285_gb300 import catalogs, ops
+    L, M = wl.lmax, wl.nmodes
+    res = {"F": [], "mixed_value": [], "mixed_kernel_ms": [], "fp32_value": [],
+           "speedup_vs_fp32": [], "unit": "columns x " + UNIT}
+    for F in (1, 4, 8):
+        x, phi, W = catalogs.weight_columns(wl, F)
+        n = x.shape[0]
+        xd, pd, Wd = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (x, phi, W))
+        ms, kms, _ = time_columns(plan, xd, pd, Wd, "mixed", reps=1)
+        v = F * n * M / (ms / 1e3)  # column x point x mode throughput
+        f32 = fp32_value
+        if F == 4:
+            fms, _, _ = time_columns(plan, xd, pd, Wd, "fp32", reps=1, warm=0)
+            f32 = F * n * M / (fms / 1e3)
+        res["F"].append(F)
+        res["mixed_value"].append(v)
+        res["mixed_kernel_ms"].append(kms)
+        res["fp32_value"].append(f32)
+        res["speedup_vs_fp32"].append(v / f32)
+        del xd, pd, Wd
+    res["fp32_value_note"] = ("F = 1 and 8: the catalog-form FP32 measurement of this line (the plain "
+                                        "path runs one transform per column); F = 4: measured through "
+                                        "pointsht_alm_columns with POINTSHT_FP32")
+    # accuracy of the mixed path (the workload's field as one column) on the bench sample
+    if sample is not None:
+        smp, ref = sample
+        xs = np.concatenate([c[0] for c in smp]).astype(np.float32)
+        ps = np.concatenate([c[1] for c in smp]).astype(np.float32)
+        ws_ = np.concatenate([(c[2].astype(np.float64) * c[3]) for c in smp]).astype(np.float32)
+        a = ops.alm_columns(plan, torch.from_numpy(xs).to(dev), torch.from_numpy(ps).to(dev),
+                            torch.from_numpy(ws_[None, :].copy()).to(dev), "mixed").cpu().numpy()[0]
+        tot = oracle.cl(ref, ref, L)
+        res["mixed_cl_err_vs_fp64_oracle"] = float(np.max(np.abs(oracle.cl(a, a, L)[1:] - tot[1:]) / tot[1:]))
+        res["mixed_alm_rel_err_per_l"] = oracle.rel_err_per_l(a, ref, L)
+    res["fp32_cl_err_vs_fp64_oracle"] = fp32_cl_err
+    # FP64 path (catalog form) on the first 1% of every catalog
+    sub = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v[:max(1, c.n // 100)].astype(np.float64))).to(dev)
+                     for v in (c.x, c.phi, c.w)), c.field, c.coeff) for c in wl.catalogs]
+    nsub = sum(int(c.x.shape[0]) for c in sub)
+    ops.alm_raw(plan, sub, wl.nfield, "fp64")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ops.alm_raw(plan, sub, wl.nfield, "fp64")
+    e1.record()
+    torch.cuda.synchronize()
+    res["fp64_value"] = nsub * M / (e0.elapsed_time(e1) / 1e3)
+    res["fp64_sample_points"] = nsub
+    res["mixed_vs_fp64"] = [v / res["fp64_value"] for v in res["mixed_value"]]
+    return res
+
+
+def ours_columns(args):
+    """F weight columns on the workload's point set through pointsht_alm_columns
+    (jackknife columns of the field: column 0 the field, column k the field with
+    the k-th of F-1 azimuthal wedges removed), then shot noise, C_l of all
+    column pairs and bandpowers.  value = F x points x modes / s."""
+    import numpy as np
+    import torch
+
+    from paper_2312_12285_gb300 import catalogs, ops
+    from paper_2312_12285_gb300.sharding import allreduce_sum, shard_array as shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = args.precision if args.precision in ("mixed", "fp32") else "mixed"
+    F = max(1, args.columns)
+    wl = load_workload(args)
+    L, M = wl.lmax, wl.nmodes
+    x, phi, W = catalogs.weight_columns(wl, F)
+    xs, ps = shard(x, rank, world), shard(phi, rank, world)
+    Ws = np.ascontiguousarray(np.stack([shard(W[f], rank, world) for f in range(F)]))
+    n_rank = xs.shape[0]
+    xd, pd, Wd = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (xs, ps, Ws))
+    plan = ops.get_plan(L, dev)
+    ws = torch.empty(max(256, ops.workspace_bytes_columns(plan, n_rank, F, prec)), dtype=torch.uint8, device=dev)
+    wsn = torch.empty(512 * F + 256, dtype=torch.uint8, device=dev)
+    out = torch.empty((F, M), dtype=torch.complex128, device=dev)
+    edges = torch.from_numpy(catalogs.log_bin_edges(L, 32).astype(np.int32)).to(dev)
+
+    def step(xd=xd, pd=pd, Wd=Wd):
+        a = ops.alm_columns(plan, xd, pd, Wd, prec, out=out, workspace=ws)
+        noise = ops.shot_noise_raw([ops.Cat(xd, pd, Wd[f], f, 1.0) for f in range(F)], F, "fp32", dev, workspace=wsn)
+        if dist is not None:
+            allreduce_sum([a, noise])
+        cl = ops.cl_raw(a, noise)
+        return cl, ops.bin_raw(cl, edges)
+
+    npass = (F + 7) // 8
+    # mixed: hist, scan, pad, scatter + (analysis, reduce) per pass; fp32: pads, hist, scan, scatter, analysis,
+    # reduce; then 2 x shot noise, C_l, bins
+    launches_per_step = (4 + 2 * npass + 4) if prec == "mixed" else (6 + 4)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in evk:
+        a_.record()
+        b_.record()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0.record()
+    for k in range(args.steps):
+        plan.set_timing_events(evk[k][0], evk[k][1])
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    plan.set_timing_events(None, None)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    kms = sum(a.elapsed_time(b) for a, b in evk) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms, kms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kms = float(t[0]), float(t[1])
+    plan.check()
+    total = F * wl.npoints * M
+    value = total / (ms / 1e3)
+    peaks = measured_peaks()
+    if prec == "mixed":
+        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        src = ("measured bf16_tflops_sustained (MEASURED_PEAKS.json; fp16 has the bf16 rate)" if bf16 else
+               "fallback 1.7 PFLOP/s sustained bf16 (fp16 has the bf16 rate)")
+        bf16 = bf16 or 1700.0
+        per_pass = [min(8, F - 8 * i) for i in range(npass)]
+        achieved = sum(mixed_mma_flops_per_point_mode(c) for c in per_pass) * n_rank * M / (kms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16,
+                "traffic": None, "kernel": "analysis_mixed_kernel (mma.sync m16n8k16 fp16 hi+lo, FP32 recurrence)",
+                "kernel_ms": kms, "peak_source": src,
+                "note": "tensor flops issued (hi x hi + lo x hi + hi x lo products, 16-row MMAs); the kernel is "
+                        "bound by the FP32 recurrence and the fp16 split on the FP32/ALU pipes, not by the tensor pipe"}
+    else:
+        props = torch.cuda.get_device_properties(dev)
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        achieved = FLOPS_PER_POINT_MODE * F * n_rank * M / (kms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "analysis_kernel (FP32)", "kernel_ms": kms,
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+
+    e2e = None
+    if not args.no_e2e:
+        hx, hp, hW = (torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in (xs, ps, Ws))
+        cl_h = torch.empty((F * (F + 1) // 2, L + 1), dtype=torch.float64).pin_memory()
+        cb_h = torch.empty((F * (F + 1) // 2, 32), dtype=torch.float64).pin_memory()
+        dx, dp, dW = torch.empty_like(xd), torch.empty_like(pd), torch.empty_like(Wd)
+
+        def e2e_step():
+            dx.copy_(hx, non_blocking=True)
+            dp.copy_(hp, non_blocking=True)
+            dW.copy_(hW, non_blocking=True)
+            cl, cb = step(dx, dp, dW)
+            cl_h.copy_(cl, non_blocking=True)
+            cb_h.copy_(cb, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        s1.record()
+        torch.cuda.synchronize()
+        ems = s0.elapsed_time(s1) / args.steps
+        if dist is not None:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t[0])
+        h2d = sum(t.numel() * t.element_size() for t in (hx, hp, hW))
+        e2e = {"value": total / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int((cl_h.numel() + cb_h.numel()) * 8), "ms_per_step": ems}
+
+    cpu = None
+    accuracy = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        target = args.cpu_sample * M if args.cpu_sample else (1.2e10 if L >= 1024 else 1e9)
+        npts = max(1, int(target / M / F))
+        t0 = time.perf_counter()
+        refs = [oracle.alm(x[:npts], phi[:npts], W[f, :npts], L) for f in range(F)]
+        dt = time.perf_counter() - t0
+        cpu = {"value": F * npts * M / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {npts} points of the point set, {F} weight columns, all {M} modes, {dt:.1f} s"}
+        a = ops.alm_columns(plan, torch.from_numpy(x[:npts].copy()).to(dev), torch.from_numpy(phi[:npts].copy()).to(dev),
+                            torch.from_numpy(np.ascontiguousarray(W[:, :npts])).to(dev), prec).cpu().numpy()
+        errs = []
+        for f in range(F):
+            tot = oracle.cl(refs[f], refs[f], L)
+            errs.append(float(np.max(np.abs(oracle.cl(a[f], a[f], L)[1:] - tot[1:]) / tot[1:])))
+        accuracy = {"cl_err_vs_fp64_oracle": max(errs),
+                    "alm_rel_err_per_l": max(oracle.rel_err_per_l(a[f], refs[f], L) for f in range(F)),
+                    "sample_points": npts,
+                    "definition": "max over columns and 1<=l<=lmax of |C_l - C_l^ref| / C_l^ref"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f16 hi+lo, f32 acc" if prec == "mixed" else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(wl, args) + f", {F} weight columns (jackknife: the field, and "
+                                                              f"the field minus each of {max(1, F - 1)} azimuthal "
+                                                              f"wedges)",
+                       "points": wl.npoints, "lmax": L, "nmodes": M, "columns": F,
+                       "l2": "inputs larger than L2", "value_counts": "columns x points x modes",
+                       "parallelism": f"points sharded over {world} GPU(s), one all-reduce of a_lm"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -410,6 +704,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.columns > 0 or args.precision == "mixed":
+        ours_columns(args)
     else:
         ours(args)
 

@@ -220,9 +220,9 @@ pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog
  *   the tensor cores with both operands split into fp16 hi + lo parts
  *   (hi*hi + lo*hi + hi*lo, FP32 accumulation, FP64 sums over chunks).  Each
  *   column is scaled by a power of two so that max|w| lies in [1, 2) (exact,
- *   undone in FP64).  Up to 4 columns share one pass; more columns take
- *   further passes over the prepared points.  lmax is limited by the shared
- *   memory of one CTA (EINVAL beyond, about lmax 3100 on sm_103).
+ *   undone in FP64).  Up to 8 columns share one pass; more columns take
+ *   further passes over the prepared points.  lmax <= 4096 (the FP32
+ *   recurrence's range, as for POINTSHT_FP32).
  * - POINTSHT_FP32: the same result through pointsht_alm with one catalog and
  *   field per column (the plain FP32 path, for comparison).
  * x, phi: device, n floats; w: device, ncol*n floats (column-major: column f

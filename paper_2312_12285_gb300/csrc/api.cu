@@ -40,6 +40,7 @@ size_t mixed_smem_bytes(int);
 int mixed_tile_points();
 int mixed_max_columns();
 int mixed_geometry_arrays();
+int64_t mixed_acc_stride(int);
 cudaError_t launch_mixed_prep(const PrepColsParams&, int64_t, cudaStream_t);
 cudaError_t launch_mixed(const MixedParams&, int, cudaStream_t);
 }  // namespace psht
@@ -538,8 +539,9 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
 // Workspace of the mixed column form.
 struct ColLayout {
     int64_t ntot = 0, chunk = 0, nunits = 0, nranges = 0;
-    int32_t nchunk = 0, npairs = 0, ncolp = 0;
-    size_t pts_off = 0, colmax_off = 0, hist_off = 0, slots_off = 0, counter_off = 0, total = 0;
+    int32_t nchunk = 0, npairs = 0, ncolp = 0, maxctas = 0;
+    int64_t accstride = 0;
+    size_t pts_off = 0, colmax_off = 0, hist_off = 0, slots_off = 0, acc_off = 0, counter_off = 0, total = 0;
 };
 
 static void make_col_layout(pointsht_plan plan, int64_t n, int32_t ncol, ColLayout& c) {
@@ -567,6 +569,11 @@ static void make_col_layout(pointsht_plan plan, int64_t n, int32_t ncol, ColLayo
     b += up256((size_t)std::max<int64_t>(c.nranges, 1) * SORT_BUCKETS * 8);
     c.slots_off = b;
     b += up256((size_t)c.ncolp * c.nchunk * plan->nmodes * 16);
+    // FP32 accumulator rows of each resident CTA (L2-resident; at most two per SM)
+    c.maxctas = 2 * plan->sm_count;
+    c.accstride = mixed_acc_stride(L);
+    c.acc_off = b;
+    b += up256((size_t)c.maxctas * c.accstride * 4);
     c.counter_off = b;
     b += 256;
     c.total = b;
@@ -586,14 +593,6 @@ static pointsht_status check_columns(pointsht_plan plan, const float* x, const f
     if (plan->lmax > F32Scale::MAX_LMAX)
         return fail(POINTSHT_EINVAL, "%s: the FP32 recurrence supports lmax <= %d (plan has %d)", who,
                     F32Scale::MAX_LMAX, plan->lmax);
-    if (prec == POINTSHT_MIXED) {
-        int optin = 0;
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device) != cudaSuccess)
-            return fail(POINTSHT_ECUDA, "%s: cannot query shared memory per block", who);
-        if (mixed_smem_bytes(plan->lmax) > (size_t)optin)
-            return fail(POINTSHT_EINVAL, "%s: lmax=%d needs %zu bytes of shared memory per CTA in the mixed path (%d available)",
-                        who, plan->lmax, mixed_smem_bytes(plan->lmax), optin);
-    }
     return POINTSHT_OK;
 }
 
@@ -709,6 +708,9 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
             mp.log2c_hi = plan->log2c_hi;
             mp.log2c_lo = plan->log2c_lo;
             mp.slots = reinterpret_cast<double*>(ws + c.slots_off);
+            mp.accg = reinterpret_cast<float*>(ws + c.acc_off);
+            mp.accstride = c.accstride;
+            mp.maxctas = c.maxctas;
             mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
             mp.err = plan->err;
             if (plan->ev_start && col0 == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));

@@ -202,6 +202,9 @@ struct MixedParams {
     const float* log2c_hi;
     const float* log2c_lo;
     double* slots;            // [col][chunk][nmodes] complex
+    float* accg;              // per-CTA FP32 accumulator rows, accstride floats each
+    int64_t accstride;
+    int32_t maxctas, pad2_;   // CTAs the accumulator buffer provides for
     int* counter;
     unsigned* err;
 };

@@ -23,8 +23,9 @@
 // warp, 4 per lane as two f32x2 pairs).  Every 32 steps the warps' partial
 // sums meet in shared memory and are added, in warp order, to the CTA's FP32
 // accumulator rows (deterministic); rows are flushed to FP64 slots per chunk.
-// Rounds of 8 steps are software-pipelined: the recurrence of round r runs
-// while the MMAs of round r - 1 are in flight.  Points still below the FP32
+// Rounds of 8 steps are software-pipelined: the MMAs of round r - 1 are issued
+// together with the recurrence of round r, and their sums stored one round
+// later, so the tensor-core latency is covered by FP32 work.  Points still below the FP32
 // range contribute nothing: their hi part is masked to zero and their lo part
 // multiplied by zero in the split itself, and a warp whose points are all
 // below range skips the split and the MMAs (its partial sums are exact zeros).
@@ -42,7 +43,7 @@ constexpr int MX_WARPS = 8;
 constexpr int MX_KQ = 4;                       // points per lane
 constexpr int MX_PW = 32 * MX_KQ;              // points per warp (128)
 constexpr int MX_P = MX_WARPS * MX_PW;         // points per tile (1024)
-constexpr int MX_MAXCOL = 4;                   // weight columns per pass
+constexpr int MX_MAXCOL = 8;                   // weight columns per pass (kernels for 4 and 8)
 constexpr int MX_NGEO = 5;                     // x, lsh, lsl, turn hi, turn lo
 constexpr int MX_BLK = 32;                     // steps between CTA combines
 
@@ -154,6 +155,16 @@ __device__ __forceinline__ void mx_mma(float (&d)[4], uint32_t a0, uint32_t a1, 
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// the same with a zero accumulator (first product of a chain)
+__device__ __forceinline__ void mx_mma0(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                        uint32_t b0, uint32_t b1) {
+    const float z = 0.f;
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(z));
+}
+
 // exponent e with max|w| * 2^-e in [1, 2) (0 for an all-zero column)
 __device__ __forceinline__ int mx_col_exp(unsigned bits) {
     if (bits == 0u) return 0;
@@ -162,46 +173,108 @@ __device__ __forceinline__ int mx_col_exp(unsigned bits) {
 }
 
 // ------------------------------------------------------------ kernel --
+// One round: 8 recurrence steps of the lane's 4 points (two f32x2 pairs; point
+// k = 2 kp + {0: .x, 1: .y}); with SPLIT each value v is also split into
+//   hi  = v with its low 13 mantissa bits cleared (exact in fp16), 0 below range
+//   lo' = hi - v (the negated low part, exact in FP32, rounded to fp16), 0 below range
+// packed as fp16 pairs of consecutive steps.
+template <bool SPLIT>
+__device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&x2)[2], float2 (&p1)[2],
+                                         float2 (&p2)[2], const float2 (&nal)[2], const uint32_t (&mask)[4],
+                                         uint32_t (&hi)[4][4], uint32_t (&lo)[4][4]) {
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+        const float4 av4 = alr[j2];
+        const float2 av0 = make_float2(av4.x, av4.y), av1 = make_float2(av4.z, av4.w);
+        float2 s0[2];
+#pragma unroll
+        for (int kp = 0; kp < 2; ++kp) {
+            const float2 sg = mx_fma2(av0, mx_mul2(x2[kp], p1[kp]), p2[kp]);
+            p2[kp] = p1[kp];
+            p1[kp] = sg;
+            s0[kp] = sg;
+        }
+#pragma unroll
+        for (int kp = 0; kp < 2; ++kp) {
+            const float2 sg = mx_fma2(av1, mx_mul2(x2[kp], p1[kp]), p2[kp]);
+            p2[kp] = p1[kp];
+            p1[kp] = sg;
+        }
+        if (SPLIT) {
+#pragma unroll
+            for (int kp = 0; kp < 2; ++kp) {
+                const float hax = __uint_as_float(__float_as_uint(s0[kp].x) & mask[2 * kp]);
+                const float hay = __uint_as_float(__float_as_uint(s0[kp].y) & mask[2 * kp + 1]);
+                const float hbx = __uint_as_float(__float_as_uint(p1[kp].x) & mask[2 * kp]);
+                const float hby = __uint_as_float(__float_as_uint(p1[kp].y) & mask[2 * kp + 1]);
+                const float2 la = mx_fma2(s0[kp], nal[kp], make_float2(hax, hay));
+                const float2 lb = mx_fma2(p1[kp], nal[kp], make_float2(hbx, hby));
+                hi[2 * kp][j2] = mx_pack(hax, hbx);
+                hi[2 * kp + 1][j2] = mx_pack(hay, hby);
+                lo[2 * kp][j2] = mx_pack(la.x, lb.x);
+                lo[2 * kp + 1][j2] = mx_pack(la.y, lb.y);
+            }
+        }
+    }
+}
+
+// fp16 hi / lo of one float: hi = round-to-nearest fp16, lo = the remainder
+__device__ __forceinline__ void mx_split_w(float v, float& h, float& l) {
+    h = __half2float(__float2half_rn(v));
+    l = v - h;
+}
+
+// NF = weight columns per pass (4 or 8).  NF = 4: A rows 0..7 = W_hi of fields
+// 0..3 (re, im), rows 8..15 = W_lo of the same; per 16-point group
+//   D1 += A . B_hi,   D2 += [W_hi; 0] . B_lo'
+// and row g of the result is (D1 - D2)[g] + D1[g + 8].  NF = 8: rows 0..15 =
+// fields 0..7 (re, im); A_hi and A_lo are separate fragments and
+//   D1 += A_hi . B_hi + A_lo . B_hi,   D2 += A_hi . B_lo',   result D1 - D2.
+template <int NF>
 __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const __grid_constant__ MixedParams p) {
-    constexpr int ARR = MX_P * 4;  // bytes of one array in a tile
+    constexpr int NV = 2 * NF;                 // values per l: (field, re/im)
+    constexpr int PS = NV + 4;                 // row stride of the partial sums (bank-conflict-free stores)
+    constexpr int AR = NF == 4 ? 4 : 8;        // A registers per 16-point group
+    constexpr int ITEMS = MX_BLK * NV / (MX_WARPS * 32);  // combine items per thread
+    constexpr int ARR = MX_P * 4;              // bytes of one array in a tile
     const int narr = MX_NGEO + p.ncol;
-    const int TILE = narr * ARR;
     const int L = p.lmax;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int64_t* s_unit = reinterpret_cast<int64_t*>(smem + 16);
-    unsigned char* tiles = smem + 128;
-    uint4* stage = reinterpret_cast<uint4*>(tiles + 2 * (MX_NGEO + MX_MAXCOL) * ARR);  // [warp][plane][128]
-    float2* phs = reinterpret_cast<float2*>(stage + MX_WARPS * 2 * MX_PW);               // [warp][128]
-    float* part = reinterpret_cast<float*>(phs + MX_WARPS * MX_PW);                      // [2][warp][32][8]
-    float* acc = part + 2 * MX_WARPS * MX_BLK * 8;                                       // [(L+2)][8]
+    unsigned char* tile = smem + 128;
+    uint4* stage = reinterpret_cast<uint4*>(tile + (MX_NGEO + NF) * ARR);  // [warp][plane][128]
+    float2* phs = reinterpret_cast<float2*>(stage + MX_WARPS * 2 * MX_PW);  // [warp][128]
+    float* part = reinterpret_cast<float*>(phs + MX_WARPS * MX_PW);         // [2][warp][32][PS]
+    if ((int)blockIdx.x >= p.maxctas) return;
+    float* accg = p.accg + (int64_t)blockIdx.x * p.accstride;               // [(L+2)][NV], this CTA's
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, c4 = lane & 3;
     const int qbase = warp * MX_PW;
     uint4* my_stage = stage + warp * 2 * MX_PW;
     float2* my_ph = phs + warp * MX_PW;
-    const uint32_t stage_addr = smem_u32(my_stage);
-    const uint32_t ld_addr = stage_addr + (uint32_t)(((lane >> 4) * MX_PW + (lane & 15)) * 16);
+    const uint32_t ld_addr = smem_u32(my_stage) + (uint32_t)(((lane >> 4) * MX_PW + (lane & 15)) * 16);
 
-    // this lane's A rows are field g >> 1: its column scale
-    const int myf = g >> 1;
-    const float wscale = myf < p.ncol ? ldexpf(1.f, -mx_col_exp(p.colmax[myf])) : 0.f;
+    // fields of this lane's A rows and their column scales
+    const int comp = g & 1;
+    const int fa = g >> 1;
+    const int fb = NF == 4 ? fa : 4 + (g >> 1);
+    const float sca = fa < p.ncol ? ldexpf(1.f, -mx_col_exp(p.colmax[fa])) : 0.f;
+    const float scb = fb < p.ncol ? ldexpf(1.f, -mx_col_exp(p.colmax[fb])) : 0.f;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t parity0 = 0, parity1 = 0;
+    uint32_t parity = 0;
 
     for (;;) {
         if (threadIdx.x == 0) s_unit[0] = (int64_t)atomicAdd(p.counter, 1);
         __syncthreads();
         const int64_t u = s_unit[0];
-        __syncthreads();
         if (u >= p.nunits) break;
         const int64_t r = u / p.npairs;
         const int pi = (int)(u - r * p.npairs);
@@ -210,47 +283,39 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
         const int ntiles = (int)(npts / MX_P);
         const int ma = pi, mb = L - pi;
         const bool single = ma == mb;
+        const int ncols = single ? 1 : 2;
         const int lena = L - ma + 1, lenb = single ? 0 : L - mb + 1;
-        for (int i = threadIdx.x; i < (lena + lenb) * 8; i += blockDim.x) acc[i] = 0.f;
+        for (int i = threadIdx.x; i < (lena + lenb) * NV; i += blockDim.x) accg[i] = 0.f;
         bool first_flush = true;
-        __syncthreads();
 
-        auto issue = [&](int t, int b) {
-            uint64_t* bar = &bars[b];
-            unsigned char* dst = tiles + b * TILE;
+        auto issue = [&](int t) {
             mbar_expect_tx(bar, narr * ARR);
             const int64_t first = pt0 + (int64_t)t * MX_P;
-            for (int a = 0; a < MX_NGEO; ++a) bulk_g2s(dst + a * ARR, p.pts + (int64_t)a * p.ntot + first, ARR, bar);
+            for (int a = 0; a < MX_NGEO; ++a) bulk_g2s(tile + a * ARR, p.pts + (int64_t)a * p.ntot + first, ARR, bar);
             for (int f = 0; f < p.ncol; ++f)
-                bulk_g2s(dst + (MX_NGEO + f) * ARR, p.wcols + (int64_t)f * p.ntot + first, ARR, bar);
+                bulk_g2s(tile + (MX_NGEO + f) * ARR, p.wcols + (int64_t)f * p.ntot + first, ARR, bar);
         };
-        if (threadIdx.x == 0 && ntiles > 0) issue(0, 0);
+        __syncthreads();  // s_unit read, accumulator rows zeroed
+        if (threadIdx.x == 0 && ntiles > 0) issue(0);
 
         for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
-            if (threadIdx.x == 0 && t + 1 < ntiles) issue(t + 1, b ^ 1);
-            const uint32_t par = b ? parity1 : parity0;
-            const bool ok = mbar_wait_bounded(&bars[b], par);
-            if (b) parity1 ^= 1u;
-            else parity0 ^= 1u;
+            const bool ok = mbar_wait_bounded(bar, parity);
+            parity ^= 1u;
             if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) {
-                    atomicOr(p.err, ERR_TIMEOUT);
-                    if (t + 1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], b ? parity0 : parity1);
-                }
+                if (threadIdx.x == 0) atomicOr(p.err, ERR_TIMEOUT);
                 return;
             }
-            const float* tf = reinterpret_cast<const float*>(tiles + b * TILE);
-            const uint32_t* tu = reinterpret_cast<const uint32_t*>(tf);
+            const float* tf = reinterpret_cast<const float*>(tile);
+            const uint32_t* tu = reinterpret_cast<const uint32_t*>(tile);
 
-            for (int col = 0; col < (single ? 1 : 2); ++col) {
+            for (int col = 0; col < ncols; ++col) {
                 const int m = col ? mb : ma;
                 const int len = L - m + 1;
-                float* cacc = acc + (col ? lena : 0) * 8;
+                float* cacc = accg + (col ? lena : 0) * NV;
                 const float2* alpha2 = p.alpha2 + p.colstart[m];
                 const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
                 // ---- per-point seed, phase and state (4 points per lane) ----
-                float2 x2[2], p1[2], p2[2], alive[2];
+                float2 x2[2], p1[2], p2[2], nal[2];
                 uint32_t mask[4];
                 int E[4];
 #pragma unroll
@@ -261,180 +326,220 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     phase_f32(m, tu[3 * MX_P + i], tu[4 * MX_P + i], cs, sn);
                     my_ph[q] = make_float2(cs, sn);
                     const float xv = tf[i];
-                    const float al = E[k] == 0 ? 1.f : 0.f;
+                    const float na = E[k] == 0 ? -1.f : 0.f;
                     if (k & 1) {
                         x2[k >> 1].y = xv;
                         p2[k >> 1].y = mant;
                         p1[k >> 1].y = 0.f;
-                        alive[k >> 1].y = al;
+                        nal[k >> 1].y = na;
                     } else {
                         x2[k >> 1].x = xv;
                         p2[k >> 1].x = mant;
                         p1[k >> 1].x = 0.f;
-                        alive[k >> 1].x = al;
+                        nal[k >> 1].x = na;
                     }
                     mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
                 }
                 __syncwarp();
-                // ---- A fragments: W^T hi (rows 0..7) and lo (rows 8..15) per 16-point group ----
-                uint32_t A[8][4];
-                {
-                    const int comp = g & 1;
+                // ---- A fragments ----
+                uint32_t A[8][AR];
 #pragma unroll
-                    for (int gi = 0; gi < 8; ++gi) {
-                        float hv[4], lv[4];
+                for (int gi = 0; gi < 8; ++gi) {
+                    float ha[4], la[4], hb[4], lb[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
-                            float wv = 0.f;
-                            if (myf < p.ncol) {
-                                const float2 ph = my_ph[q];
-                                const float w = tf[(MX_NGEO + myf) * MX_P + qbase + q] * wscale;
-                                wv = comp ? -w * ph.y : w * ph.x;
-                            }
-                            hv[e] = __half2float(__float2half_rn(wv));
-                            lv[e] = wv - hv[e];
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
+                        const float2 ph = my_ph[q];
+                        const float trig = comp ? -ph.y : ph.x;
+                        const float wa = fa < p.ncol ? tf[(MX_NGEO + fa) * MX_P + qbase + q] * sca * trig : 0.f;
+                        mx_split_w(wa, ha[e], la[e]);
+                        if (NF == 8) {
+                            const float wb = fb < p.ncol ? tf[(MX_NGEO + fb) * MX_P + qbase + q] * scb * trig : 0.f;
+                            mx_split_w(wb, hb[e], lb[e]);
                         }
-                        A[gi][0] = mx_pack(hv[0], hv[1]);
-                        A[gi][1] = mx_pack(lv[0], lv[1]);
-                        A[gi][2] = mx_pack(hv[2], hv[3]);
-                        A[gi][3] = mx_pack(lv[2], lv[3]);
                     }
+                    if (NF == 4) {
+                        A[gi][0] = mx_pack(ha[0], ha[1]);
+                        A[gi][1] = mx_pack(la[0], la[1]);
+                        A[gi][2] = mx_pack(ha[2], ha[3]);
+                        A[gi][3] = mx_pack(la[2], la[3]);
+                    } else {
+                        A[gi][0] = mx_pack(ha[0], ha[1]);
+                        A[gi][1] = mx_pack(hb[0], hb[1]);
+                        A[gi][2] = mx_pack(ha[2], ha[3]);
+                        A[gi][3] = mx_pack(hb[2], hb[3]);
+                        A[gi][AR / 2 + 0] = mx_pack(la[0], la[1]);
+                        A[gi][AR / 2 + 1] = mx_pack(lb[0], lb[1]);
+                        A[gi][AR / 2 + 2] = mx_pack(la[2], la[3]);
+                        A[gi][AR / 2 + 3] = mx_pack(lb[2], lb[3]);
+                    }
+                }
+                if (col == ncols - 1) {
+                    // every warp has read the tile: fetch the next one behind this column
+                    __syncthreads();
+                    if (threadIdx.x == 0 && t + 1 < ntiles) issue(t + 1);
                 }
                 bool lane_neg = (E[0] | E[1] | E[2] | E[3]) != 0;
                 bool any_neg = __any_sync(0xffffffffu, lane_neg);
-                // a warp all of whose points are still below the FP32 range
-                // contributes exact zeros: it runs the recurrence only
+                // a warp all of whose points are still below range contributes
+                // exact zeros: it runs the recurrence only
                 bool warp_alive = __any_sync(0xffffffffu, (E[0] == 0) | (E[1] == 0) | (E[2] == 0) | (E[3] == 0));
                 const int nrounds = 4 * ((len + MX_BLK - 1) / MX_BLK);
-                // Software pipeline over rounds of 8 steps: round r's
-                // recurrence and split run while round r-1's MMAs are in
-                // flight; round r-1's sums are stored after that.
-                float Da[4], Db[4], Dc[4], Dd[4];
-                bool act_prev = false;
-                for (int r = 0; r <= nrounds; ++r) {
-                    const bool have = r < nrounds;
-                    const bool act = have && warp_alive;
-                    uint32_t hi[4][4], lo[4][4];
-                    if (have) {
-                        const float4* a4 = reinterpret_cast<const float4*>(alpha2 + 8 * r);
+                float D1[4], D2[4];
+                float accv[ITEMS];
+                // recurrence coefficients of the next round, loaded one round ahead
+                float4 aln[4];
 #pragma unroll
-                        for (int j2 = 0; j2 < 4; ++j2) {
-                            const float4 av4 = __ldg(a4 + j2);
-                            const float2 av[2] = {make_float2(av4.x, av4.y), make_float2(av4.z, av4.w)};
-                            float2 s0[2];
+                for (int j = 0; j < 4; ++j) aln[j] = __ldg(reinterpret_cast<const float4*>(alpha2) + j);
+                // Rounds of 8 steps in a three-stage pipeline.  Iteration r8:
+                //   store the sums of round r8-2 (its MMAs were issued one iteration ago),
+                //   load the B fragments of round r8-1 and issue its MMAs in the same
+                //   basic block as round r8's recurrence and split, so that the MMA
+                //   latency is covered by FP32 work, then stage round r8.
+                bool mm_prev = false;  // round r8-2 had its MMAs issued
+                bool st_prev = false;  // round r8-1 is staged
+                for (int r8 = 0; r8 < nrounds + 2; ++r8) {
+                    if (r8 >= 2) {
+                        // round r8-2: columns l = 8 (r8-2) + 2 c4 (+1) of this order
+                        const int rp = r8 - 2;
+                        float* pb = part + ((rp >> 2) & 1) * (MX_WARPS * MX_BLK * PS);
+                        const int row = warp * MX_BLK + 8 * (rp & 3) + 2 * c4;
+                        if (NF == 4) {
+                            pb[row * PS + g] = mm_prev ? (D1[0] - D2[0]) + D1[2] : 0.f;
+                            pb[(row + 1) * PS + g] = mm_prev ? (D1[1] - D2[1]) + D1[3] : 0.f;
+                        } else {
 #pragma unroll
-                            for (int jj = 0; jj < 2; ++jj) {
-#pragma unroll
-                                for (int kp = 0; kp < 2; ++kp) {
-                                    const float2 sg = mx_fma2(av[jj], mx_mul2(x2[kp], p1[kp]), p2[kp]);
-                                    p2[kp] = p1[kp];
-                                    p1[kp] = sg;
-                                }
-                                if (jj == 0) {
-                                    s0[0] = p1[0];
-                                    s0[1] = p1[1];
-                                }
-                            }
-                            if (act) {
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const float va = (k & 1) ? s0[k >> 1].y : s0[k >> 1].x;
-                                    const float vb = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
-                                    const float al = (k & 1) ? alive[k >> 1].y : alive[k >> 1].x;
-                                    const float ha = __uint_as_float(__float_as_uint(va) & mask[k]);
-                                    const float hb = __uint_as_float(__float_as_uint(vb) & mask[k]);
-                                    hi[k][j2] = mx_pack(ha, hb);
-                                    lo[k][j2] = mx_pack(fmaf(va, al, -ha), fmaf(vb, al, -hb));
-                                }
-                            }
+                            for (int e = 0; e < 4; ++e)
+                                pb[(row + (e & 1)) * PS + (e >> 1) * 8 + g] = mm_prev ? D1[e] - D2[e] : 0.f;
                         }
-                        if (any_neg && (r & 1)) {
-                            // rescale check every 16 steps (F32Scale: 2^64 blocks)
-                            lane_neg = false;
+                        if ((rp & 3) == 3) {
+                            // block rp/4 complete in every warp: add the warps'
+                            // partial sums, in warp order
+                            __syncthreads();
+                            const int bk = rp >> 2;
+                            const float* pbb = part + (bk & 1) * (MX_WARPS * MX_BLK * PS);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
-                                float& bb = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
-                                const bool nd = (E[k] < 0) & (fmaxf(fabsf(a), fabsf(bb)) > 0x1p-61f);
-                                const float sc = nd ? 0x1p-64f : 1.f;
-                                a *= sc;
-                                bb *= sc;
-                                E[k] += nd;
-                                mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
-                                if (k & 1) alive[k >> 1].y = E[k] == 0 ? 1.f : 0.f;
-                                else alive[k >> 1].x = E[k] == 0 ? 1.f : 0.f;
-                                lane_neg |= E[k] != 0;
+                            for (int j = 0; j < ITEMS; ++j) {
+                                const int it = threadIdx.x + j * MX_WARPS * 32;
+                                const int li = it / NV, v = it % NV;
+                                const int q = MX_BLK * bk + li;
+                                if (q < len) {
+                                    float sacc = accv[j];
+#pragma unroll
+                                    for (int w = 0; w < MX_WARPS; ++w) sacc += pbb[(w * MX_BLK + li) * PS + v];
+                                    cacc[q * NV + v] = sacc;
+                                }
                             }
-                            any_neg = __any_sync(0xffffffffu, lane_neg);
-                            warp_alive = __any_sync(0xffffffffu, (E[0] == 0) | (E[1] == 0) | (E[2] == 0) | (E[3] == 0));
                         }
                     }
-                    if (r >= 1) {
-                        // round r-1: row g (W_hi terms) + row g + 8 (W_lo terms),
-                        // columns l = 8 (r-1) + 2 c4 (+1) of the column
-                        const int rp = r - 1;
-                        float* pb = part + ((rp >> 2) & 1) * (MX_WARPS * MX_BLK * 8);
-                        const int row = warp * MX_BLK + 8 * (rp & 3) + 2 * c4;
-                        pb[row * 8 + g] = act_prev ? ((Da[0] + Db[0]) + (Dc[0] + Dd[0])) + (Da[2] + Db[2]) : 0.f;
-                        pb[(row + 1) * 8 + g] = act_prev ? ((Da[1] + Db[1]) + (Dc[1] + Dd[1])) + (Da[3] + Db[3]) : 0.f;
-                        if ((r & 3) == 0) {
-                            // block (r-1)/4 complete in every warp: add the
-                            // warps' partial sums in warp order
-                            __syncthreads();
-                            const int bk = (r >> 2) - 1;
-                            const int li = threadIdx.x >> 3, v = threadIdx.x & 7;  // 32 l x 8 values
-                            const int q = MX_BLK * bk + li;
-                            if (q < len) {
-                                const float* pbb = part + (bk & 1) * (MX_WARPS * MX_BLK * 8);
-                                float sacc = cacc[q * 8 + v];
+                    if ((r8 & 3) == 2 && r8 - 2 < nrounds) {
+                        // accumulator rows of block (r8-2)/4, read ahead of its combine
 #pragma unroll
-                                for (int w = 0; w < MX_WARPS; ++w) sacc += pbb[(w * MX_BLK + li) * 8 + v];
-                                cacc[q * 8 + v] = sacc;
+                        for (int j = 0; j < ITEMS; ++j) {
+                            const int it = threadIdx.x + j * MX_WARPS * 32;
+                            const int q = MX_BLK * ((r8 - 2) >> 2) + it / NV;
+                            accv[j] = q < len ? cacc[q * NV + it % NV] : 0.f;
+                        }
+                    }
+                    const bool have = r8 < nrounds;
+                    const bool act = have && warp_alive;
+                    const bool mm = st_prev;
+                    uint32_t bf[8][4];
+                    if (mm) {
+#pragma unroll
+                        for (int gi = 0; gi < 8; ++gi)
+                            mx_ldsm_x4_t(ld_addr + (uint32_t)(16 * gi * 16), bf[gi][0], bf[gi][1], bf[gi][2], bf[gi][3]);
+                    }
+                    __syncwarp();  // every lane has read the stage before it is rewritten
+                    float4 alr[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) alr[j] = aln[j];
+                    if (r8 + 1 < nrounds) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            aln[j] = __ldg(reinterpret_cast<const float4*>(alpha2 + 8 * (r8 + 1)) + j);
+                    }
+                    uint32_t hi[4][4], lo[4][4];
+                    auto mmas = [&]() {
+#pragma unroll
+                        for (int gi = 0; gi < 8; ++gi) {
+                            if (NF == 4) {
+                                if (gi == 0) {
+                                    mx_mma0(D1, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][0], bf[gi][1]);
+                                    mx_mma0(D2, A[gi][0], 0u, A[gi][2], 0u, bf[gi][2], bf[gi][3]);
+                                } else {
+                                    mx_mma(D1, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][0], bf[gi][1]);
+                                    mx_mma(D2, A[gi][0], 0u, A[gi][2], 0u, bf[gi][2], bf[gi][3]);
+                                }
+                            } else {
+                                if (gi == 0) {
+                                    mx_mma0(D1, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][0], bf[gi][1]);
+                                    mx_mma0(D2, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][2], bf[gi][3]);
+                                } else {
+                                    mx_mma(D1, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][0], bf[gi][1]);
+                                    mx_mma(D2, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bf[gi][2], bf[gi][3]);
+                                }
+                                mx_mma(D1, A[gi][AR / 2], A[gi][AR / 2 + 1], A[gi][AR / 2 + 2], A[gi][AR / 2 + 3],
+                                       bf[gi][0], bf[gi][1]);
                             }
                         }
+                    };
+                    if (mm && act) {
+                        mmas();
+                        mx_round<true>(alr, x2, p1, p2, nal, mask, hi, lo);
+                    } else if (act) {
+                        mx_round<true>(alr, x2, p1, p2, nal, mask, hi, lo);
+                    } else {
+                        if (mm) mmas();
+                        if (have) mx_round<false>(alr, x2, p1, p2, nal, mask, hi, lo);
                     }
                     if (act) {
-                        __syncwarp();  // every lane has read the previous round's stage
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             my_stage[32 * k + lane] = make_uint4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
                             my_stage[MX_PW + 32 * k + lane] = make_uint4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
                         }
-                        __syncwarp();
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) Da[e] = Db[e] = Dc[e] = Dd[e] = 0.f;
-#pragma unroll
-                        for (int gi = 0; gi < 8; ++gi) {
-                            uint32_t bh0, bh1, bl0, bl1;
-                            mx_ldsm_x4_t(ld_addr + (uint32_t)(16 * gi * 16), bh0, bh1, bl0, bl1);
-                            if (gi & 1) {
-                                mx_mma(Db, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bh0, bh1);
-                                mx_mma(Dd, A[gi][0], 0u, A[gi][2], 0u, bl0, bl1);
-                            } else {
-                                mx_mma(Da, A[gi][0], A[gi][1], A[gi][2], A[gi][3], bh0, bh1);
-                                mx_mma(Dc, A[gi][0], 0u, A[gi][2], 0u, bl0, bl1);
-                            }
-                        }
                     }
-                    act_prev = act;
+                    __syncwarp();  // the stage is complete before the next iteration reads it
+                    if (have && any_neg && (r8 & 1)) {
+                        // rescale check every 16 steps (F32Scale: 2^64 blocks)
+                        lane_neg = false;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
+                            float& b = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
+                            const bool nd = (E[k] < 0) & (fmaxf(fabsf(a), fabsf(b)) > 0x1p-61f);
+                            const float sc = nd ? 0x1p-64f : 1.f;
+                            a *= sc;
+                            b *= sc;
+                            E[k] += nd;
+                            mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
+                            if (k & 1) nal[k >> 1].y = E[k] == 0 ? -1.f : 0.f;
+                            else nal[k >> 1].x = E[k] == 0 ? -1.f : 0.f;
+                            lane_neg |= E[k] != 0;
+                        }
+                        any_neg = __any_sync(0xffffffffu, lane_neg);
+                        warp_alive = __any_sync(0xffffffffu, (E[0] == 0) | (E[1] == 0) | (E[2] == 0) | (E[3] == 0));
+                    }
+                    mm_prev = mm;
+                    st_prev = act;
                 }
                 __syncthreads();  // the column's rows are complete; phases may be rewritten
             }
             // ---- flush the accumulator rows into this chunk's FP64 slots ----
             if (t == ntiles - 1 || (t + 1) % p.flush_tiles == 0) {
-                for (int i = threadIdx.x; i < (lena + lenb) * 8; i += blockDim.x) {
-                    const int q = i >> 3, v = i & 7;
+                for (int i = threadIdx.x; i < (lena + lenb) * NV; i += blockDim.x) {
+                    const int q = i / NV, v = i % NV;
                     const int f = v >> 1;
                     if (f < p.ncol) {
                         const int m = q < lena ? ma : mb;
                         const int l = q < lena ? ma + q : mb + (q - lena);
                         double* sp =
                             p.slots + (((int64_t)f * p.nchunk + r) * p.nmodes + tri_base(m, L) + l) * 2 + (v & 1);
-                        const double val = ldexp((double)acc[i], mx_col_exp(p.colmax[f]));
+                        const double val = ldexp((double)accg[i], mx_col_exp(p.colmax[f]));
                         *sp = (first_flush ? 0.0 : *sp) + val;
                     }
-                    acc[i] = 0.f;
+                    accg[i] = 0.f;
                 }
                 first_flush = false;
             }
@@ -444,15 +549,16 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
 }
 
 // ------------------------------------------------------------ launchers --
-size_t mixed_smem_bytes(int lmax) {
-    const size_t accf = (size_t)(lmax + 2) * 8;
-    return 128 + 2 * (size_t)(MX_NGEO + MX_MAXCOL) * MX_P * 4 + (size_t)MX_WARPS * 2 * MX_PW * 16 +
-           (size_t)MX_WARPS * MX_PW * 8 + (size_t)2 * MX_WARPS * MX_BLK * 8 * 4 + accf * 4;
+size_t mixed_smem_bytes(int nf) {
+    return 128 + (size_t)(MX_NGEO + nf) * MX_P * 4 + (size_t)MX_WARPS * 2 * MX_PW * 16 + (size_t)MX_WARPS * MX_PW * 8 +
+           (size_t)2 * MX_WARPS * MX_BLK * (2 * nf + 4) * 4;
 }
 
 int mixed_tile_points() { return MX_P; }
 int mixed_max_columns() { return MX_MAXCOL; }
 int mixed_geometry_arrays() { return MX_NGEO; }
+// floats of one CTA's accumulator rows (the widest pass, 2 x MX_MAXCOL values per l)
+int64_t mixed_acc_stride(int lmax) { return ((int64_t)(lmax + 2) * 2 * MX_MAXCOL + 63) / 64 * 64; }
 
 cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStream_t st) {
     mx_pad_kernel<<<64, 256, 0, st>>>(pp);
@@ -463,15 +569,20 @@ cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStr
 }
 
 cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
-    const size_t smem = mixed_smem_bytes(mp.lmax);
+    const int nf = mp.ncol <= 4 ? 4 : 8;
+    const size_t smem = mixed_smem_bytes(nf);
+    const void* kern = nf == 4 ? reinterpret_cast<const void*>(analysis_mixed_kernel<4>)
+                               : reinterpret_cast<const void*>(analysis_mixed_kernel<8>);
     int occ = 0;
-    cudaError_t e = configure_kernel(reinterpret_cast<const void*>(analysis_mixed_kernel), MX_WARPS * 32, smem, &occ);
+    cudaError_t e = configure_kernel(kern, MX_WARPS * 32, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * occ;
     if (grid > mp.nunits) grid = mp.nunits;
+    if (grid > mp.maxctas) grid = mp.maxctas;
     if (grid < 1) grid = 1;
-    analysis_mixed_kernel<<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    if (nf == 4) analysis_mixed_kernel<4><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    else analysis_mixed_kernel<8><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
     return cudaGetLastError();
 }
 

@@ -44,33 +44,38 @@ def _columns(dev, x, phi, W, L, precision="mixed"):
     return out.cpu().numpy()
 
 
+NONZERO = (0, 1, 2, 3, 5, 6, 7, 8, 9)
+
+
 @pytest.fixture(scope="module")
 def small(dev):
-    """25 000 points (24 full tiles and a ragged one) at lmax 256, six columns
-    (two passes: 4 + 2): the signed FKP field, plain weights, weights of order
-    1e-6 and 1e5 (column scaling), all zeros, and galaxies only."""
+    """25 000 points (24 full tiles and a ragged one) at lmax 256, ten columns
+    (two passes: 8 columns, then 2 with the 4-column kernel): the signed FKP
+    field, plain weights, weights of order 1e-6 and 1e5 (column scaling), all
+    zeros, galaxies only, and four jackknife columns of the FKP field."""
     L = 256
     wl = catalogs.lognormal_cap(2_500, 22_500, L, config_id=31, nwaves=64, grid=(128, 256))
-    x, phi, W1 = catalogs.weight_columns(wl, 1)
+    x, phi, Wj = catalogs.weight_columns(wl, 5)
     n = x.shape[0]
     assert n == 25_000
     rng = catalogs.rng_for(31, 5)
     ng = wl.catalogs[0].n
-    W = np.zeros((6, n), np.float32)
-    W[0] = W1[0]
+    W = np.zeros((10, n), np.float32)
+    W[0] = Wj[0]
     W[1] = rng.uniform(0.8, 1.2, n)
     W[2] = rng.uniform(0.0, 1.0, n) * 1e-6
     W[3] = rng.standard_normal(n) * 1e5
     W[5, :ng] = wl.catalogs[0].w
+    W[6:10] = Wj[1:5]
     got = _columns(dev, x, phi, W, L)
     x64, p64 = x.astype(np.float64), phi.astype(np.float64)
-    ref = [oracle.alm(x64, p64, W[f].astype(np.float64), L) if f != 4 else None for f in range(6)]
+    ref = [oracle.alm(x64, p64, W[f].astype(np.float64), L) if f in NONZERO else None for f in range(10)]
     return L, x, phi, W, got, ref
 
 
 def test_mixed_matches_oracle(small):
     L, _, _, _, got, ref = small
-    for f in (0, 1, 2, 3, 5):
+    for f in NONZERO:
         assert oracle.rel_err_per_l(got[f], ref[f], L) <= TOL_CL, f
         assert _cl_err(got[f], ref[f], L) <= TOL_CL, f
 
@@ -83,24 +88,33 @@ def test_zero_column_is_exactly_zero(small):
 def test_mixed_matches_plain_fp32_columns(small, dev):
     L, x, phi, W, got, _ = small
     f32 = _columns(dev, x, phi, W, L, "fp32")
-    for f in (0, 1, 2, 3, 5):
+    for f in NONZERO:
         assert _cl_err(got[f], f32[f], L) <= TOL_CL, f
 
 
+@pytest.mark.parametrize("cols", [[5], [0, 5, 9], [1, 2, 3, 5, 6]])
+def test_column_result_independent_of_pass_shape(small, dev, cols):
+    """A column gives the same a_lm (to FP32 accumulation rounding) whether it
+    runs alone, in a 4-column pass or in an 8-column pass."""
+    L, x, phi, W, got, _ = small
+    g = _columns(dev, x, phi, W[cols], L)
+    for j, f in enumerate(cols):
+        assert oracle.rel_err_per_l(g[j], got[f], L) <= 1e-6, f
+
+
 def test_power_of_two_scaling_is_exact(small, dev):
-    """Columns are rescaled by powers of two only: w * 2^20 gives exactly
-    2^20 times the a_lm of w (and w * 2^-30 exactly 2^-30 times)."""
+    """Columns are rescaled by powers of two only: in the same pass layout,
+    w * 2^20 gives exactly 2^20 times the a_lm of w (and w * 2^-30 exactly
+    2^-30 times), and the other columns are unchanged bit for bit."""
     L, x, phi, W, got, _ = small
-    W2 = np.stack([W[1] * np.float32(2.0 ** 20), W[1] * np.float32(2.0 ** -30)])
+    W2 = W.copy()
+    W2[1] *= np.float32(2.0 ** 20)
+    W2[6] *= np.float32(2.0 ** -30)
     g2 = _columns(dev, x, phi, W2, L)
-    assert np.array_equal(g2[0], got[1] * 2.0 ** 20)
-    assert np.array_equal(g2[1], got[1] * 2.0 ** -30)
-
-
-def test_single_column_equals_column_in_a_pass(small, dev):
-    L, x, phi, W, got, _ = small
-    g1 = _columns(dev, x, phi, W[5:6], L)
-    assert oracle.rel_err_per_l(g1[0], got[5], L) <= 1e-6
+    assert np.array_equal(g2[1], got[1] * 2.0 ** 20)
+    assert np.array_equal(g2[6], got[6] * 2.0 ** -30)
+    for f in (0, 2, 3, 4, 5, 7, 8, 9):
+        assert np.array_equal(g2[f], got[f]), f
 
 
 def test_run_to_run_bitwise(small, dev):
@@ -152,12 +166,11 @@ def test_out_of_range_point_is_flagged(dev):
 
 
 def test_argument_errors(dev):
-    plan = ops.get_plan(4000, dev)
     x = torch.zeros(8, dtype=torch.float32, device=dev)
     w = torch.ones((1, 8), dtype=torch.float32, device=dev)
     with pytest.raises(_lib.PointSHTError) as ei:
-        ops.alm_columns(plan, x, x, w, "mixed")
-    assert ei.value.status == _lib.EINVAL and "shared memory" in str(ei.value)
+        ops.alm_columns(ops.get_plan(4097, dev), x, x, w, "mixed")  # beyond the FP32 recurrence's range
+    assert ei.value.status == _lib.EINVAL and "lmax" in str(ei.value)
     with pytest.raises(_lib.PointSHTError):
         ops.alm_columns(ops.get_plan(32, dev), x, x, w, "fp64")
 
