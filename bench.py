@@ -406,7 +406,11 @@ def ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)", "kernel_ms": kms,
                          "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
-                                        f"{sm_max:.0f} MHz (recipe unit counts and clock)"},
+                                        f"{sm_max:.0f} MHz (recipe unit counts and clock)",
+                         "ncu_pipe": {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
+                                      "source": "profiles/analysis_kernel_lognormal_cap_1e5pts_l2048_full.md "
+                                                "(same kernel and launch shape, 1e5-point case: these counters "
+                                                "take 3 ncu passes, so they are not captured at full size)"}},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
