@@ -57,6 +57,10 @@ def _load():
             lib.oracle_alm.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_hermite_basis.argtypes = [ctypes.c_double, dp]
+            lib.oracle_hermite_basis.restype = None
+            lib.oracle_alm_interp.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+            lib.oracle_alm_interp.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -249,3 +253,25 @@ def rel_err_per_l(a, ref, lmax: int):
         den[m:] += np.abs(ref[sl]) ** 2
     r = np.sqrt(num[1:] / np.maximum(den[1:], 1e-300))
     return float(np.max(r)) if lmax >= 1 else 0.0
+
+
+# ------------------------------------------- interpolated transform (App.) --
+def hermite_basis(t: float) -> np.ndarray:
+    """Cubic Hermite basis c_0..c_3 at t in [0, 1] (App. "Interpolation")."""
+    out = np.zeros(4, np.float64)
+    _load().oracle_hermite_basis(float(t), _dptr(out))
+    return out
+
+
+def alm_interp(x, phi, w, lmax: int, ntheta: int, nthreads: int = 0):
+    """a_lm by the paper's interpolation route with ntheta samples equispaced
+    in theta (s_k = (k + 1/2) pi / ntheta, ghost samples continued across the
+    poles): full packed triangle, complex128."""
+    lib = _load()
+    x, phi, w = _f64(x), _f64(phi), _f64(w)
+    out = np.zeros(2 * nmodes(lmax), np.float64)
+    rc = lib.oracle_alm_interp(x.shape[0], _dptr(x), _dptr(phi), _dptr(w), int(lmax), int(ntheta), _dptr(out),
+                               int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_alm_interp failed ({rc})")
+    return out[0::2] + 1j * out[1::2]

@@ -264,3 +264,172 @@ int oracle_adjoint(int64_t n, const double* x, const double* phi, int lmax,
     }
     return status;
 }
+
+/* ------------------------------------------------ interpolated transform --
+ * The paper's interpolation route (App. "Interpolation"): the smooth
+ * y_lm = lambda_lm(cos theta) is known exactly (value and derivative, App. A)
+ * on a set of sample points only, and each point's y_lm is the cubic Hermite
+ * spline through its two neighbouring samples.  Because the spline is linear
+ * in the sampled values, the sum over points is done first, per order m:
+ *
+ *   v^(m)_{j alpha} = sum_r w_r e^{-i m phi_r} c_{j alpha}(r)
+ *   a_lm = sum_j [v_j0 y(s_j) + v_j1 h y'(s_j) + v_j2 y(s_{j+1}) + v_j3 h y'(s_{j+1})]
+ *
+ * with c_0 = (2t+1)(1-t)^2, c_1 = t(1-t)^2, c_2 = t^2(3-2t), c_3 = t^2(t-1).
+ *
+ * Reading (the paper samples in x = cos theta and treats |x| > 3/4 apart):
+ * here the samples are equispaced in theta, s_k = (k + 1/2) h, h = pi/N,
+ * k = 0..N-1, and y' is the theta-derivative.  In theta, y_lm is smooth up to
+ * and through the poles once it is continued across them as the function on
+ * the great circle, y(-theta) = (-1)^m y(theta) (the point (-theta, phi) is
+ * (theta, phi + pi)), and likewise at theta = pi; the two outermost intervals
+ * use ghost samples at -h/2 and pi + h/2 given by that continuation, so no
+ * point needs separate treatment.  The theta-derivative follows from App. A's
+ * derivative of Pbar: d/dtheta = -sin(theta) d/dx,
+ *   dPbar_l/dtheta = [l x Pbar_l - (l+m) sqrt((l-m)/(l+m)) Pbar_{l-1}] / sin(theta).
+ * All arithmetic in FP64; sums over points and samples Neumaier-compensated. */
+
+/* Hermite basis of the interpolation section at parameter t in [0, 1]. */
+void oracle_hermite_basis(double t, double* c) {
+    c[0] = (2.0 * t + 1.0) * (1.0 - t) * (1.0 - t);
+    c[1] = t * (1.0 - t) * (1.0 - t);
+    c[2] = t * t * (3.0 - 2.0 * t);
+    c[3] = t * t * (t - 1.0);
+}
+
+/* Interval of a point: theta = arccos(x), u = theta/h - 1/2, j = floor(u)
+ * clamped to [-1, N-1] (left sample j, right sample j+1), t = u - j.       */
+static void interp_interval(double x, int ntheta, int* j_out, double* t_out) {
+    double xc = x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
+    double h = ORACLE_PI / (double)ntheta;
+    double u = acos(xc) / h - 0.5;
+    int j = (int)floor(u);
+    if (j < -1) j = -1;
+    if (j > ntheta - 1) j = ntheta - 1;
+    double t = u - (double)j;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    *j_out = j;
+    *t_out = t;
+}
+
+/* y_lm(s_k) and h dy_lm/dtheta(s_k) for l = m..lmax at every sample k, as
+ * [k][l-m] arrays.                                                          */
+static void interp_samples(int ntheta, int lmax, int m, const double* c1, const double* c2, double* ys, double* ds,
+                           double* mant, int* expo) {
+    const int len = lmax - m + 1;
+    const double h = ORACLE_PI / (double)ntheta;
+    for (int k = 0; k < ntheta; ++k) {
+        double th = (k + 0.5) * h;
+        double x = cos(th), s = sin(th);
+        pbar_column_scaled(x, lmax, m, c1, c2, mant, expo);
+        double prev = 0.0; /* Pbar_{l-1}^m */
+        for (int l = m; l <= lmax; ++l) {
+            double p = ldexp(mant[l - m], expo[l - m]);
+            double dp = (double)l * x * p;
+            if (l > m) dp -= (double)(l + m) * sqrt((double)(l - m) / (double)(l + m)) * prev;
+            dp /= s;
+            double nrm = sqrt((2.0 * l + 1.0) / (4.0 * ORACLE_PI));
+            ys[(size_t)k * len + (l - m)] = nrm * p;
+            ds[(size_t)k * len + (l - m)] = nrm * h * dp;
+            prev = p;
+        }
+    }
+}
+
+/* Interpolated a_lm (full packed triangle, interleaved re/im) of one weighted
+ * point set with N = ntheta samples in theta.  Returns 0, -1 (bad argument)
+ * or -2 (allocation).                                                       */
+int oracle_alm_interp(int64_t n, const double* x, const double* phi, const double* w, int lmax, int ntheta,
+                      double* out, int nthreads) {
+    if (n < 0 || lmax < 0 || ntheta < 2) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int* jr = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double* cr = (double*)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    if (!jr || !cr) {
+        free(jr); free(cr);
+        return -2;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+        double t;
+        interp_interval(x[r], ntheta, &jr[r], &t);
+        oracle_hermite_basis(t, cr + 4 * r);
+    }
+    int status = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int m = 0; m <= lmax; ++m) {
+        const int len = lmax - m + 1;
+        const int nb = ntheta + 1; /* intervals j = -1..N-1 */
+        double* c1 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* c2 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* mant = (double*)malloc(sizeof(double) * (size_t)len);
+        int* expo = (int*)malloc(sizeof(int) * (size_t)len);
+        double* ys = (double*)malloc(sizeof(double) * (size_t)ntheta * len);
+        double* ds = (double*)malloc(sizeof(double) * (size_t)ntheta * len);
+        nsum* v = (nsum*)calloc((size_t)nb * 8, sizeof(nsum));  /* [interval][alpha][re, im] */
+        nsum* vy = (nsum*)calloc((size_t)ntheta * 2, sizeof(nsum));
+        nsum* vd = (nsum*)calloc((size_t)ntheta * 2, sizeof(nsum));
+        if (!c1 || !c2 || !mant || !expo || !ys || !ds || !v || !vy || !vd) {
+#pragma omp critical
+            status = -2;
+        } else {
+            pbar_coeffs(lmax, m, c1, c2);
+            interp_samples(ntheta, lmax, m, c1, c2, ys, ds, mant, expo);
+            /* v^(m)_{j alpha}: sum over points, within their interval */
+            for (int64_t r = 0; r < n; ++r) {
+                double ph = (double)m * phi[r];
+                double wc = w[r] * cos(ph), ws = -w[r] * sin(ph);
+                nsum* vb = v + (size_t)(jr[r] + 1) * 8;
+                for (int a = 0; a < 4; ++a) {
+                    nsum_add(&vb[2 * a], cr[4 * r + a] * wc);
+                    nsum_add(&vb[2 * a + 1], cr[4 * r + a] * ws);
+                }
+            }
+            /* per sample: left-sample terms of its interval, right-sample terms
+             * of the previous one; the ghosts fold onto the end samples */
+            const double sg = (m & 1) ? -1.0 : 1.0;
+            for (int b = 0; b < nb; ++b) {
+                const int j = b - 1;
+                for (int ri = 0; ri < 2; ++ri) {
+                    double v0 = nsum_val(&v[(size_t)b * 8 + 0 + ri]), v1 = nsum_val(&v[(size_t)b * 8 + 2 + ri]);
+                    double v2 = nsum_val(&v[(size_t)b * 8 + 4 + ri]), v3 = nsum_val(&v[(size_t)b * 8 + 6 + ri]);
+                    if (j >= 0) {
+                        nsum_add(&vy[2 * j + ri], v0);
+                        nsum_add(&vd[2 * j + ri], v1);
+                    } else {
+                        nsum_add(&vy[0 + ri], sg * v0);
+                        nsum_add(&vd[0 + ri], -sg * v1);
+                    }
+                    if (j + 1 <= ntheta - 1) {
+                        nsum_add(&vy[2 * (j + 1) + ri], v2);
+                        nsum_add(&vd[2 * (j + 1) + ri], v3);
+                    } else {
+                        nsum_add(&vy[2 * (ntheta - 1) + ri], sg * v2);
+                        nsum_add(&vd[2 * (ntheta - 1) + ri], -sg * v3);
+                    }
+                }
+            }
+            const int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+            for (int q = 0; q < len; ++q) {
+                nsum re = {0.0, 0.0}, im = {0.0, 0.0};
+                for (int k = 0; k < ntheta; ++k) {
+                    double y = ys[(size_t)k * len + q], d = ds[(size_t)k * len + q];
+                    nsum_add(&re, nsum_val(&vy[2 * k]) * y);
+                    nsum_add(&re, nsum_val(&vd[2 * k]) * d);
+                    nsum_add(&im, nsum_val(&vy[2 * k + 1]) * y);
+                    nsum_add(&im, nsum_val(&vd[2 * k + 1]) * d);
+                }
+                out[2 * (base + m + q)] = nsum_val(&re);
+                out[2 * (base + m + q) + 1] = nsum_val(&im);
+            }
+        }
+        free(c1); free(c2); free(mant); free(expo); free(ys); free(ds); free(v); free(vy); free(vd);
+    }
+    free(jr);
+    free(cr);
+    return status;
+}
