@@ -36,6 +36,7 @@ METRIC = "a_lm points*modes/s at lmax=2048, mixed vs FP64 at C_l err 1e-4; roofl
 UNIT = "points*modes/s"
 FLOPS_PER_POINT_MODE = 7  # recurrence: 1 mul + 1 FMA; accumulation: 2 FMA (Sec. 2.2 / App. A)
 FP32_LANES_PER_SM = 128
+FP64_TFLOPS_NOMINAL = 1.25
 
 
 def parse():
@@ -320,7 +321,14 @@ def ours(args):
     except Exception:
         pass
     sm_max = sm_max or 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s FP32
+    if prec == "fp64":
+        # FP64 pipe: the nominal dense FP64 rate of the part (profiling recipe's table)
+        peak = FP64_TFLOPS_NOMINAL
+        peak_src = "nominal GB300 FP64 1.25 TFLOP/s (recipe table; a DFMA loop measured 1.18)"
+    else:
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s FP32
+        peak_src = (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                    f"(recipe unit counts and clock)")
     achieved = FLOPS_PER_POINT_MODE * n_rank * wl.nmodes / (kms / 1e3) / 1e12
     traffic = profiled_traffic(wl.name, n_rank)
 
@@ -404,10 +412,11 @@ def ours(args):
                        "cuda_graph": bool(gstep is not None)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)", "kernel_ms": kms,
-                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
-                                        f"{sm_max:.0f} MHz (recipe unit counts and clock)",
-                         "ncu_pipe": {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
+                         "kernel": ("analysis_kernel (FP64, 4 points/lane, 4 warps/CTA)" if prec == "fp64" else
+                                    "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)"),
+                         "kernel_ms": kms,
+                         "peak_source": peak_src,
+                         "ncu_pipe": None if prec == "fp64" else {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
                                       "source": "profiles/analysis_kernel_lognormal_cap_1e5pts_l2048_full.md "
                                                 "(same kernel and launch shape, 1e5-point case: these counters "
                                                 "take 3 ncu passes, so they are not captured at full size)"}},

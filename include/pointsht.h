@@ -236,6 +236,34 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
                                      int64_t n, int32_t ncol, pointsht_precision prec, double* alm_out,
                                      void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- Interpolated transform (the paper's fast route) -------------------
+ * a_lm of each field by App. "Interpolation": y_lm = lambda_lm(cos theta) and
+ * its theta-derivative are evaluated exactly (App. A) on ntheta samples
+ * equispaced in theta, s_k = (k + 1/2) pi/ntheta, and each point takes the
+ * cubic Hermite spline of its interval; the sum over points runs first, per
+ * order m (binning of w e^{-i m phi} times the 4 spline weights into the
+ * intervals), then a transform of the samples (the mixed tensor-core kernel
+ * on three weight columns per sample) and an FP64 combination.  The samples
+ * are in theta, not in x as in the paper: in theta y_lm stays smooth through
+ * the poles when continued across them (y(-theta) = (-1)^m y(theta)), so the
+ * two outer intervals use ghost samples and no point is treated apart.
+ * Error: the spline's O(h^4) interpolation error, about 2e-5 relative per
+ * value at ntheta = 8 lmax and 1.5e-6 at 16 lmax (h = pi/ntheta), plus the
+ * mixed path's rounding; work O(N lmax + ntheta lmax^2) instead of
+ * O(N lmax^2).
+ * cats as for pointsht_alm with float x, phi, w (POINTSHT_FP32 layout);
+ * ntheta even, 2 <= ntheta <= 32768; fewer than 2^31 points per field;
+ * alm_out: device, nfield*M complex128; workspace: device, >=
+ * pointsht_workspace_size_interp() bytes (~(lmax+1)(ntheta+1) x 56 bytes:
+ * 3.8 GB at lmax 2048, ntheta 32768), 256-byte aligned, clobbered.
+ * Errors as for pointsht_alm. */
+size_t pointsht_workspace_size_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                      int32_t nfield, int32_t ntheta);
+
+pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                    int32_t nfield, int32_t ntheta, double* alm_out, void* workspace,
+                                    size_t ws_bytes, void* stream);
+
 /* Size of the fixed scratch array used by pointsht_alm_noalloc (64 MiB). */
 #define POINTSHT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

@@ -26,6 +26,7 @@ EXPORTS = (
     "pointsht_shot_noise", "pointsht_combine", "pointsht_cl", "pointsht_cl_backward", "pointsht_bin",
     "pointsht_bin_backward", "pointsht_alm_backward", "pointsht_alm_noalloc",
     "pointsht_workspace_size_columns", "pointsht_alm_columns",
+    "pointsht_workspace_size_interp", "pointsht_alm_interp",
 )
 
 
@@ -79,6 +80,8 @@ def load(build_if_missing: bool = True):
             "pointsht_alm_noalloc": ([vp, cp, i32, i32, ctypes.c_int, dp, vp], ctypes.c_int),
             "pointsht_workspace_size_columns": ([vp, i64, i32, ctypes.c_int], sz),
             "pointsht_alm_columns": ([vp, vp, vp, vp, i64, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),
+            "pointsht_workspace_size_interp": ([vp, cp, i32, i32, i32], sz),
+            "pointsht_alm_interp": ([vp, cp, i32, i32, i32, dp, vp, sz, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

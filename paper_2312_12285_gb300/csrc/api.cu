@@ -43,6 +43,10 @@ int mixed_geometry_arrays();
 int64_t mixed_acc_stride(int);
 cudaError_t launch_mixed_prep(const PrepColsParams&, int64_t, cudaStream_t);
 cudaError_t launch_mixed(const MixedParams&, int, cudaStream_t);
+int64_t interp_nranges(int64_t);
+cudaError_t launch_interp_sort(const InterpParams&, cudaStream_t);
+cudaError_t launch_interp_tables(const InterpParams&, int, cudaStream_t);
+cudaError_t launch_interp_combine(int, int64_t, const double*, double*, cudaStream_t);
 }  // namespace psht
 
 using namespace psht;
@@ -731,6 +735,192 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
         rp.out = alm_out + (size_t)col0 * plan->nmodes * 2;
         cudaError_t e = launch_reduce(rp, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: reduce launch: %s", cudaGetErrorString(e));
+    }
+    return POINTSHT_OK;
+}
+
+// ------------------------------------------------------ interpolated --
+struct InterpLayout {
+    int64_t npts_max = 0, nranges_max = 0, ntot = 0, chunk = 0, nunits = 0;
+    int32_t nb = 0, nchunk = 0, npairs = 0, maxctas = 0;
+    int64_t accstride = 0;
+    size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, v_off = 0, wtab_off = 0,
+           nodes_off = 0, colmax_off = 0, slots_off = 0, acc_off = 0, counter_off = 0, T_off = 0, total = 0;
+};
+
+static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                               int32_t ntheta, InterpLayout& c) {
+    const int L = plan->lmax;
+    const int P = mixed_tile_points();
+    for (int f = 0; f < nfield; ++f) {
+        int64_t n = 0, nr = 0;
+        for (int k = 0; k < ncat; ++k)
+            if (cats[k].field == f) {
+                n += cats[k].n;
+                nr += interp_nranges(cats[k].n);
+            }
+        c.npts_max = std::max(c.npts_max, n);
+        c.nranges_max = std::max(c.nranges_max, nr);
+    }
+    c.nb = ntheta + 1;
+    c.ntot = ((int64_t)ntheta + P - 1) / P * P;
+    c.npairs = L / 2 + 1;
+    const int64_t target = (int64_t)4 * plan->sm_count;
+    int64_t chunk = P;
+    while (chunk * 2 <= ((int64_t)1 << 22)) chunk *= 2;
+    while (chunk > P && (c.ntot + chunk - 1) / chunk * c.npairs < target) chunk /= 2;
+    c.chunk = chunk;
+    c.nchunk = (int32_t)((c.ntot + chunk - 1) / chunk);
+    c.nunits = (int64_t)c.nchunk * c.npairs;
+    c.maxctas = 2 * plan->sm_count;
+    c.accstride = mixed_acc_stride(L);
+    const int64_t np = std::max<int64_t>(c.npts_max, 1);
+    size_t b = 0;
+    c.hist_off = b;   b += up256((size_t)std::max<int64_t>(c.nranges_max, 1) * c.nb * 4);
+    c.binoff_off = b; b += up256((size_t)(c.nb + 1) * 8);
+    c.total_off = b;  b += up256((size_t)c.nb * 8);
+    c.wc_off = b;     b += up256((size_t)np * 4 * 4);
+    c.turn_off = b;   b += up256((size_t)np * 2 * 4);
+    c.v_off = b;      b += up256((size_t)(L + 1) * c.nb * 4 * 8);
+    c.wtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 6 * 8);
+    c.nodes_off = b;  b += up256((size_t)c.ntot * mixed_geometry_arrays() * 4);
+    c.colmax_off = b; b += 256;
+    c.slots_off = b;  b += up256((size_t)6 * c.nchunk * plan->nmodes * 16);
+    c.acc_off = b;    b += up256((size_t)c.maxctas * c.accstride * 4);
+    c.counter_off = b; b += 256;
+    c.T_off = b;      b += up256((size_t)6 * plan->nmodes * 16);
+    c.total = b;
+}
+
+static pointsht_status check_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                    int32_t ntheta, const char* who) {
+    pointsht_status s = check_common(plan, cats, ncat, nfield, POINTSHT_FP32, who);
+    if (s != POINTSHT_OK) return s;
+    if (ntheta < 2 || ntheta > 32768 || (ntheta & 1))
+        return fail(POINTSHT_EINVAL, "%s: ntheta=%d must be even and in [2, 32768]", who, ntheta);
+    if (plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "%s: the FP32 recurrence supports lmax <= %d (plan has %d)", who,
+                    F32Scale::MAX_LMAX, plan->lmax);
+    for (int f = 0; f < nfield; ++f) {
+        int64_t n = 0;
+        for (int k = 0; k < ncat; ++k)
+            if (cats[k].field == f) n += cats[k].n;
+        if (n >= ((int64_t)1 << 31)) return fail(POINTSHT_EINVAL, "%s: field %d has 2^31 or more points", who, f);
+    }
+    return POINTSHT_OK;
+}
+
+extern "C" size_t pointsht_workspace_size_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                                 int32_t nfield, int32_t ntheta) {
+    if (check_interp(plan, cats, ncat, nfield, ntheta, "workspace_size_interp") != POINTSHT_OK) return 0;
+    InterpLayout c;
+    make_interp_layout(plan, cats, ncat, nfield, ntheta, c);
+    return c.total;
+}
+
+extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                               int32_t nfield, int32_t ntheta, double* alm_out, void* workspace,
+                                               size_t ws_bytes, void* stream) {
+    pointsht_status s = check_interp(plan, cats, ncat, nfield, ntheta, "alm_interp");
+    if (s != POINTSHT_OK) return s;
+    if (!alm_out || ((uintptr_t)alm_out % 16))
+        return fail(POINTSHT_EINVAL, "alm_interp: alm_out NULL or not 16-byte aligned");
+    if ((s = check_device(plan, "alm_interp")) != POINTSHT_OK) return s;
+    InterpLayout c;
+    make_interp_layout(plan, cats, ncat, nfield, ntheta, c);
+    if (!workspace) return fail(POINTSHT_EINVAL, "alm_interp: workspace is NULL");
+    if ((uintptr_t)workspace % 256) return fail(POINTSHT_EINVAL, "alm_interp: workspace is not 256-byte aligned");
+    if (ws_bytes < c.total)
+        return fail(POINTSHT_ENOMEM, "alm_interp: workspace has %zu bytes, %zu needed", ws_bytes, c.total);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    const int L = plan->lmax;
+    for (int f = 0; f < nfield; ++f) {
+        InterpParams ip;
+        memset(&ip, 0, sizeof(ip));
+        ip.lmax = L;
+        ip.ntheta = ntheta;
+        ip.nb = c.nb;
+        ip.ntot = c.ntot;
+        int64_t r = 0, n = 0;
+        for (int k = 0; k < ncat; ++k) {
+            if (cats[k].field != f) continue;
+            ip.cat[ip.ncat].x = static_cast<const float*>(cats[k].x);
+            ip.cat[ip.ncat].phi = static_cast<const float*>(cats[k].phi);
+            ip.cat[ip.ncat].w = static_cast<const float*>(cats[k].w);
+            ip.cat[ip.ncat].n = cats[k].n;
+            ip.cat[ip.ncat].coeff = cats[k].coeff;
+            ip.range0[ip.ncat] = r;
+            r += interp_nranges(cats[k].n);
+            n += cats[k].n;
+            ++ip.ncat;
+        }
+        ip.range0[ip.ncat] = r;
+        ip.nranges = r;
+        ip.npts = n;
+        ip.hist = reinterpret_cast<int32_t*>(ws + c.hist_off);
+        ip.binoff = reinterpret_cast<int64_t*>(ws + c.binoff_off);
+        ip.total = reinterpret_cast<int64_t*>(ws + c.total_off);
+        ip.wc = reinterpret_cast<float*>(ws + c.wc_off);
+        ip.turn = reinterpret_cast<uint32_t*>(ws + c.turn_off);
+        ip.v = reinterpret_cast<float2*>(ws + c.v_off);
+        ip.wtab = reinterpret_cast<float2*>(ws + c.wtab_off);
+        ip.nodes = reinterpret_cast<uint32_t*>(ws + c.nodes_off);
+        ip.colmax = reinterpret_cast<unsigned*>(ws + c.colmax_off);
+        ip.err = plan->err;
+        CUDA_TRY(cudaMemsetAsync(ip.colmax, 0, 256, st));
+        if (plan->ev_start && f == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
+        cudaError_t e = launch_interp_sort(ip, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: sort launch: %s", cudaGetErrorString(e));
+        e = launch_interp_tables(ip, plan->sm_count, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: binning launch: %s", cudaGetErrorString(e));
+        // grid transform of the six sample-weight columns (mixed kernel, table mode)
+        CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
+        MixedParams mp;
+        memset(&mp, 0, sizeof(mp));
+        mp.lmax = L;
+        mp.ncol = 6;
+        mp.npairs = c.npairs;
+        mp.flush_tiles = FLUSH_TILES;
+        mp.nmodes = plan->nmodes;
+        mp.chunk = c.chunk;
+        mp.nunits = c.nunits;
+        mp.ntot = c.ntot;
+        mp.nchunk = c.nchunk;
+        mp.pts = ip.nodes;
+        mp.wcols = nullptr;
+        mp.colmax = ip.colmax;
+        mp.alpha2 = plan->alpha_f2;
+        mp.colstart = plan->colstart;
+        mp.log2c_hi = plan->log2c_hi;
+        mp.log2c_lo = plan->log2c_lo;
+        mp.slots = reinterpret_cast<double*>(ws + c.slots_off);
+        mp.accg = reinterpret_cast<float*>(ws + c.acc_off);
+        mp.accstride = c.accstride;
+        mp.maxctas = c.maxctas;
+        mp.wtab = ip.wtab;
+        mp.wtab_ncol = 6;
+        mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
+        mp.err = plan->err;
+        e = launch_mixed(mp, plan->sm_count, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: grid transform launch: %s", cudaGetErrorString(e));
+        ReduceParams rp;
+        memset(&rp, 0, sizeof(rp));
+        rp.nfield = 6;
+        rp.nmodes = plan->nmodes;
+        for (int k = 0; k < 6; ++k) {
+            rp.slot0[k] = k * c.nchunk;
+            rp.nchunk[k] = c.nchunk;
+        }
+        rp.slots = reinterpret_cast<const double*>(ws + c.slots_off);
+        rp.gamma = plan->gamma;
+        rp.out = reinterpret_cast<double*>(ws + c.T_off);
+        e = launch_reduce(rp, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: reduce launch: %s", cudaGetErrorString(e));
+        e = launch_interp_combine(L, plan->nmodes, reinterpret_cast<const double*>(ws + c.T_off),
+                                  alm_out + (size_t)f * plan->nmodes * 2, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: combine launch: %s", cudaGetErrorString(e));
+        if (plan->ev_stop && f == nfield - 1) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
     }
     return POINTSHT_OK;
 }

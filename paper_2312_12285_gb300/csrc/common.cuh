@@ -204,8 +204,35 @@ struct MixedParams {
     double* slots;            // [col][chunk][nmodes] complex
     float* accg;              // per-CTA FP32 accumulator rows, accstride floats each
     int64_t accstride;
-    int32_t maxctas, pad2_;   // CTAs the accumulator buffer provides for
+    int32_t maxctas, wtab_ncol;   // CTAs the accumulator buffer provides for; columns of wtab
+    const float2* wtab;       // table mode: complex weights [(lmax+1)][ntot][wtab_ncol] instead of w e^{-i m phi}
     int* counter;
+    unsigned* err;
+};
+
+// Interpolated transform (interp.cu)
+struct InterpCat {
+    const float* x;
+    const float* phi;
+    const float* w;
+    int64_t n;
+    double coeff;
+};
+
+struct InterpParams {
+    int32_t lmax, ntheta, nb, ncat;  // nb = ntheta + 1 intervals
+    int64_t npts, nranges, ntot;     // ntot = samples padded to the grid-transform tile
+    InterpCat cat[PSHT_MAX_CATS];
+    int64_t range0[PSHT_MAX_CATS + 1];  // first range of each catalog
+    int32_t* hist;                      // [nranges][nb]: counts, then first slots
+    int64_t* binoff;                    // [nb + 1]
+    int64_t* total;                     // [nb]
+    float* wc;                          // [4][npts] w coeff c_alpha, interval order
+    uint32_t* turn;                     // [2][npts]
+    float2* v;                          // [(lmax+1)][nb][4]
+    float2* wtab;                       // [(lmax+1)][ntot][6]
+    uint32_t* nodes;                    // [5][ntot] sample geometry (x, lsh, lsl, turn hi, lo)
+    unsigned* colmax;                   // [6]
     unsigned* err;
 };
 

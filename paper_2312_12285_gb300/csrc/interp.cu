@@ -1,0 +1,381 @@
+// interp.cu -- the paper's interpolated transform (App. "Interpolation") on
+// the GPU: y_lm is sampled (value and theta-derivative) on N points
+// equispaced in theta, s_k = (k + 1/2) h, h = pi/N, each catalog point
+// interpolates it by the cubic Hermite spline of its interval, and the sum
+// over points is taken first, per order m:
+//
+//   v^(m)_{j alpha} = sum_{r in interval j} w_r e^{-i m phi_r} c_alpha(t_r)      (binning)
+//   Vy_k = v_{k,0} + v_{k-1,2},  Vd_k = v_{k,1} + v_{k-1,3}                  (fold)
+//   a_lm = sum_k [Vy_k y_lm(s_k) + h Vd_k dy_lm/dtheta(s_k)]                 (grid transform)
+//
+// The intervals j = -1 and N-1 reach ghost samples at -h/2 and pi + h/2,
+// continued across the poles as y(-theta) = (-1)^m y(theta) and
+// y'(-theta) = (-1)^(m+1) y'(theta); they fold onto samples 0 and N-1.
+// With dy/dtheta = [l x lambda_l - sqrt((l^2-m^2)(2l+1)/(2l-1)) lambda_{l-1}] / sin
+// (App. A's derivative of Pbar), the grid transform is three plain
+// transforms of the samples with the per-(m, sample) weights
+//   W0 = Vy,  W1 = h x Vd / sin,  W2 = h Vd / sin,
+//   a_lm = T0_lm + l T1_lm - c_lm T2_{l-1,m},   c_lm = sqrt((l^2-m^2)(2l+1)/(2l-1)),
+// run by the mixed tensor-core kernel in its table mode (mixed.cu) and
+// combined in FP64 here.  Polar samples (sin < 1/16) carry their W in three
+// columns of their own, so that each fp16 column scale covers a range of
+// 1/sin below 2^11 (one pass of the 8-column kernel, six columns).
+//
+// Kernels: ip_hist / ip_scan_* / ip_scatter (stable counting sort of the
+// points by interval, deterministic), ip_bin (binning, one warp per
+// (interval, block of 256 orders), lanes over m, phases by exact fixed-point
+// turns and a 32-step rotation), ip_fold (sample weights, column maxima),
+// ip_nodes (sample geometry in |x| order for the grid transform) and
+// ip_combine.
+#include "common.cuh"
+
+namespace psht {
+
+constexpr int IP_RANGE = 65536;  // points per range of the counting sort
+constexpr int IP_MCHUNK = 256;   // orders per binning task (8 per lane)
+
+// interval j (-1..N-1) and parameter t of cos(theta) = x; +1 gives the bucket
+__device__ __forceinline__ int ip_interval(float x, int ntheta, double& t) {
+    double xd = (double)x;
+    xd = xd > 1.0 ? 1.0 : (xd < -1.0 ? -1.0 : xd);
+    const double h = 3.14159265358979323846 / (double)ntheta;
+    const double u = acos(xd) / h - 0.5;
+    int j = (int)floor(u);
+    j = j < -1 ? -1 : (j > ntheta - 1 ? ntheta - 1 : j);
+    double tt = u - (double)j;
+    t = tt < 0.0 ? 0.0 : (tt > 1.0 ? 1.0 : tt);
+    return j;
+}
+
+__device__ __forceinline__ bool ip_range_of(const InterpParams& p, int64_t r, int& c, int64_t& i0, int64_t& i1) {
+    c = 0;
+    while (c + 1 < p.ncat && p.range0[c + 1] <= r) ++c;
+    i0 = (r - p.range0[c]) * IP_RANGE;
+    i1 = min(p.cat[c].n, i0 + IP_RANGE);
+    return i0 < i1;
+}
+
+__device__ __forceinline__ bool ip_valid(const InterpCat& c, int64_t i) {
+    const float x = c.x[i], ph = c.phi[i], w = c.w[i];
+    return isfinite(x) && isfinite(ph) && isfinite(w) && fabsf(x) <= 1.f;
+}
+
+// ------------------------------------------------------ counting sort --
+__global__ void __launch_bounds__(256) ip_hist_kernel(const __grid_constant__ InterpParams p) {
+    extern __shared__ int cnt[];
+    const int64_t r = blockIdx.x;
+    for (int b = threadIdx.x; b < p.nb; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    int c;
+    int64_t i0, i1;
+    if (ip_range_of(p, r, c, i0, i1)) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            double t;
+            atomicAdd(&cnt[ip_interval(p.cat[c].x[i], p.ntheta, t) + 1], 1);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < p.nb; b += blockDim.x) p.hist[r * p.nb + b] = cnt[b];
+}
+
+// per bucket: prefix over ranges (in place) and the bucket total
+__global__ void ip_scan_ranges_kernel(const __grid_constant__ InterpParams p) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nb) return;
+    int64_t run = 0;
+    for (int64_t r = 0; r < p.nranges; ++r) {
+        const int h = p.hist[r * p.nb + b];
+        p.hist[r * p.nb + b] = (int32_t)run;
+        run += h;
+    }
+    p.total[b] = run;
+}
+
+// exclusive scan of the bucket totals (one CTA)
+__global__ void __launch_bounds__(1024) ip_scan_buckets_kernel(const __grid_constant__ InterpParams p) {
+    __shared__ int64_t part[1024];
+    const int per = (p.nb + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    int64_t s = 0;
+    for (int b = b0; b < min(p.nb, b0 + per); ++b) s += p.total[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < 1024; ++k) {
+            const int64_t v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        p.binoff[p.nb] = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int b = b0; b < min(p.nb, b0 + per); ++b) {
+        p.binoff[b] = run;
+        run += p.total[b];
+    }
+}
+
+// stable scatter: one warp per range, points in index order
+__global__ void __launch_bounds__(32) ip_scatter_kernel(const __grid_constant__ InterpParams p) {
+    extern __shared__ int32_t next[];  // point counts of one field stay below 2^31 (checked on the host)
+    const int64_t r = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int b = lane; b < p.nb; b += 32) next[b] = (int32_t)(p.binoff[b] + p.hist[r * p.nb + b]);
+    __syncwarp();
+    int c;
+    int64_t i0, i1;
+    if (!ip_range_of(p, r, c, i0, i1)) return;
+    const InterpCat& cd = p.cat[c];
+    for (int64_t base = i0; base < i1; base += 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < i1;
+        double t = 0.0;
+        const int b = valid ? ip_interval(cd.x[i], p.ntheta, t) + 1 : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int64_t dst = 0;
+        if (valid) dst = next[b] + rank;
+        __syncwarp();
+        if (valid && rank == 0) next[b] += __popc(peers);
+        __syncwarp();
+        if (valid) {
+            const bool ok = ip_valid(cd, i);
+            if (!ok) atomicOr(p.err, ERR_RANGE);
+            const double wv = ok ? cd.coeff * (double)cd.w[i] : 0.0;
+            const double u = 1.0 - t;
+            p.wc[dst] = (float)(wv * (2.0 * t + 1.0) * u * u);
+            p.wc[p.npts + dst] = (float)(wv * t * u * u);
+            p.wc[2 * p.npts + dst] = (float)(wv * t * t * (3.0 - 2.0 * t));
+            p.wc[3 * p.npts + dst] = (float)(wv * t * t * (t - 1.0));
+            const uint64_t turn = phi_to_turn(ok ? (double)cd.phi[i] : 0.0);
+            p.turn[dst] = (uint32_t)(turn >> 32);
+            p.turn[p.npts + dst] = (uint32_t)(turn & 0xffffffffu);
+        }
+    }
+}
+
+// -------------------------------------------------------------- binning --
+// v^(m)_{j alpha} for one interval and 256 orders per warp: lane l holds
+// m = 256 c + l + 32 k, k = 0..7, as (re, im) of the 4 alpha.
+__global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ InterpParams p) {
+    const int lane = threadIdx.x & 31;
+    const int nch = (p.lmax + IP_MCHUNK) / IP_MCHUNK;
+    const int64_t ntask = (int64_t)p.nb * nch;
+    const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += nwarp) {
+        const int b = (int)(task / nch), c = (int)(task - (int64_t)(task / nch) * nch);
+        const int m0 = IP_MCHUNK * c + lane;
+        float vr[8][4], vi[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) vr[k][a] = vi[k][a] = 0.f;
+        const int64_t r0 = p.binoff[b], r1 = p.binoff[b + 1];
+        for (int64_t r = r0; r < r1; ++r) {
+            const float w0 = p.wc[r], w1 = p.wc[p.npts + r], w2 = p.wc[2 * p.npts + r], w3 = p.wc[3 * p.npts + r];
+            const uint32_t th = p.turn[r], tl = p.turn[p.npts + r];
+            float cs, sn, c32, s32;
+            phase_f32(m0, th, tl, cs, sn);
+            phase_f32(32, th, tl, c32, s32);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                // w c_alpha e^{-i m phi} = w c_alpha (cos - i sin)
+                vr[k][0] = fmaf(w0, cs, vr[k][0]);
+                vi[k][0] = fmaf(-w0, sn, vi[k][0]);
+                vr[k][1] = fmaf(w1, cs, vr[k][1]);
+                vi[k][1] = fmaf(-w1, sn, vi[k][1]);
+                vr[k][2] = fmaf(w2, cs, vr[k][2]);
+                vi[k][2] = fmaf(-w2, sn, vi[k][2]);
+                vr[k][3] = fmaf(w3, cs, vr[k][3]);
+                vi[k][3] = fmaf(-w3, sn, vi[k][3]);
+                const float cn = fmaf(cs, c32, -sn * s32);
+                sn = fmaf(sn, c32, cs * s32);
+                cs = cn;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int m = m0 + 32 * k;
+            if (m <= p.lmax) {
+                float4* dst = reinterpret_cast<float4*>(p.v + ((int64_t)m * p.nb + b) * 4);
+                dst[0] = make_float4(vr[k][0], vi[k][0], vr[k][1], vi[k][1]);
+                dst[1] = make_float4(vr[k][2], vi[k][2], vr[k][3], vi[k][3]);
+            }
+        }
+    }
+}
+
+// sample k -> position in the grid transform (|x| descending: both poles first)
+__device__ __forceinline__ int64_t ip_pos(int k, int ntheta) {
+    return k < ntheta / 2 ? 2 * (int64_t)k : 2 * (int64_t)(ntheta - 1 - k) + 1;
+}
+
+// sample weights W0 = Vy, W1 = h x Vd / sin, W2 = h Vd / sin (columns 0..2, or
+// 3..5 for polar samples); column maxima
+__global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ InterpParams p) {
+    const int N = p.ntheta;
+    const int64_t total = (int64_t)(p.lmax + 1) * N;
+    const double h = 3.14159265358979323846 / (double)N;
+    unsigned mx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / N), k = (int)(e - (int64_t)m * N);
+        const float2* vm = p.v + (int64_t)m * p.nb * 4;
+        // interval k (bucket k + 1): sample k is its left end; interval k - 1
+        // (bucket k): its right end
+        const float2 a0 = vm[(k + 1) * 4 + 0], a1 = vm[(k + 1) * 4 + 1];
+        const float2 b2 = vm[k * 4 + 2], b3 = vm[k * 4 + 3];
+        float2 vy = make_float2(a0.x + b2.x, a0.y + b2.y);
+        float2 vd = make_float2(a1.x + b3.x, a1.y + b3.y);
+        const float sg = (m & 1) ? -1.f : 1.f;
+        if (k == 0) {  // ghost at -h/2 = left end of interval -1 (bucket 0)
+            const float2 g0 = vm[0], g1 = vm[1];
+            vy.x += sg * g0.x;
+            vy.y += sg * g0.y;
+            vd.x -= sg * g1.x;
+            vd.y -= sg * g1.y;
+        }
+        if (k == N - 1) {  // ghost at pi + h/2 = right end of interval N-1 (bucket N)
+            const float2 g2 = vm[N * 4 + 2], g3 = vm[N * 4 + 3];
+            vy.x += sg * g2.x;
+            vy.y += sg * g2.y;
+            vd.x -= sg * g3.x;
+            vd.y -= sg * g3.y;
+        }
+        const double th = (k + 0.5) * h;
+        const double s = sin(th), x = cos(th);
+        const float f1 = (float)(h * x / s), f2 = (float)(h / s);
+        const float2 w1 = make_float2(f1 * vd.x, f1 * vd.y), w2 = make_float2(f2 * vd.x, f2 * vd.y);
+        // polar samples (sin < 1/16) in columns 3..5: 1/sin spans 2/h, more
+        // than an fp16 column scale holds; split at 1/16 each set spans < 2^11
+        const int g = s < 0.0625 ? 3 : 0;
+        float2* dst = p.wtab + ((int64_t)m * p.ntot + ip_pos(k, N)) * 6;
+        dst[g] = vy;
+        dst[g + 1] = w1;
+        dst[g + 2] = w2;
+        dst[3 - g] = make_float2(0.f, 0.f);
+        dst[4 - g] = make_float2(0.f, 0.f);
+        dst[5 - g] = make_float2(0.f, 0.f);
+        const unsigned u0 = __float_as_uint(fmaxf(fabsf(vy.x), fabsf(vy.y)));
+        const unsigned u1 = __float_as_uint(fmaxf(fabsf(w1.x), fabsf(w1.y)));
+        const unsigned u2 = __float_as_uint(fmaxf(fabsf(w2.x), fabsf(w2.y)));
+        if (g) {
+            mx[3] = max(mx[3], u0);
+            mx[4] = max(mx[4], u1);
+            mx[5] = max(mx[5], u2);
+        } else {
+            mx[0] = max(mx[0], u0);
+            mx[1] = max(mx[1], u1);
+            mx[2] = max(mx[2], u2);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        const unsigned v = __reduce_max_sync(0xffffffffu, mx[f]);
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&p.colmax[f], v);
+    }
+}
+
+// zero weights of the padding positions N..ntot-1 of every order
+__global__ void ip_pad_kernel(const __grid_constant__ InterpParams p) {
+    const int64_t npad = p.ntot - p.ntheta;
+    const int64_t total = (int64_t)(p.lmax + 1) * npad * 6;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = e / (npad * 6), rem = e - m * npad * 6;
+        p.wtab[(m * p.ntot + p.ntheta) * 6 + rem] = make_float2(0.f, 0.f);
+    }
+}
+
+// sample geometry in the layout of the mixed kernel (x, log2 sin hi/lo, turn 0)
+__global__ void ip_nodes_kernel(const __grid_constant__ InterpParams p) {
+    const int N = p.ntheta;
+    const double h = 3.14159265358979323846 / (double)N;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p.ntot; q += (int64_t)gridDim.x * blockDim.x) {
+        float x = 0.f, lh = 0.f, ll = 0.f;
+        if (q < N) {
+            const int k = (q & 1) ? N - 1 - (int)(q >> 1) : (int)(q >> 1);
+            const double th = (k + 0.5) * h;
+            const double ls = log2(sin(th));
+            x = (float)cos(th);
+            lh = (float)ls;
+            ll = (float)(ls - (double)lh);
+        }
+        float* b = reinterpret_cast<float*>(p.nodes);
+        b[q] = x;
+        b[p.ntot + q] = lh;
+        b[2 * p.ntot + q] = ll;
+        p.nodes[3 * p.ntot + q] = 0u;
+        p.nodes[4 * p.ntot + q] = 0u;
+    }
+}
+
+// a_lm = T0 + l T1 - c_lm T2_{l-1}  (T_f = grid transforms of columns f and f + 3)
+__global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, double2* out) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nmodes;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        // (l, m) of the packed m-major index m(2L+1-m)/2 + l; column m starts
+        // at start(m) = m(2L+3-m)/2
+        int m = (int)((2.0 * lmax + 3.0 - sqrt((2.0 * lmax + 3.0) * (2.0 * lmax + 3.0) - 8.0 * (double)idx)) * 0.5);
+        m = m < 0 ? 0 : (m > lmax ? lmax : m);
+        while (m > 0 && (int64_t)m * (2 * lmax + 3 - m) / 2 > idx) --m;
+        while (m < lmax && (int64_t)(m + 1) * (2 * lmax + 3 - (m + 1)) / 2 <= idx) ++m;
+        const int l = (int)(idx - (int64_t)m * (2 * lmax + 1 - m) / 2);
+        const double2 t0 = T[idx], t1 = T[nmodes + idx], u0 = T[3 * nmodes + idx], u1 = T[4 * nmodes + idx];
+        double re = (t0.x + u0.x) + (double)l * (t1.x + u1.x), im = (t0.y + u0.y) + (double)l * (t1.y + u1.y);
+        if (l > m) {
+            const double c = sqrt(((double)l * l - (double)m * m) * (2.0 * l + 1.0) / (2.0 * l - 1.0));
+            const double2 t2 = T[2 * nmodes + idx - 1], u2 = T[5 * nmodes + idx - 1];
+            re -= c * (t2.x + u2.x);
+            im -= c * (t2.y + u2.y);
+        }
+        out[idx] = make_double2(re, im);
+    }
+}
+
+// ------------------------------------------------------------ launchers --
+int64_t interp_nranges(int64_t n) { return (n + IP_RANGE - 1) / IP_RANGE; }
+
+cudaError_t launch_interp_sort(const InterpParams& p, cudaStream_t st) {
+    if (p.nranges == 0) {
+        // no points: empty intervals
+        return cudaMemsetAsync(p.binoff, 0, (size_t)(p.nb + 1) * sizeof(int64_t), st);
+    }
+    const size_t hs = (size_t)p.nb * sizeof(int);
+    int occ = 0;
+    cudaError_t e = configure_kernel(reinterpret_cast<const void*>(ip_hist_kernel), 256, hs, &occ);
+    if (e != cudaSuccess) return e;
+    ip_hist_kernel<<<(unsigned)p.nranges, 256, hs, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ip_scan_ranges_kernel<<<(p.nb + 255) / 256, 256, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ip_scan_buckets_kernel<<<1, 1024, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t ss = (size_t)p.nb * sizeof(int32_t);
+    e = configure_kernel(reinterpret_cast<const void*>(ip_scatter_kernel), 32, ss, &occ);
+    if (e != cudaSuccess) return e;
+    ip_scatter_kernel<<<(unsigned)p.nranges, 32, ss, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp_tables(const InterpParams& p, int sm_count, cudaStream_t st) {
+    ip_bin_kernel<<<sm_count * 8, 256, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ip_fold_kernel<<<sm_count * 8, 256, 0, st>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (p.ntot > p.ntheta) {
+        ip_pad_kernel<<<sm_count * 4, 256, 0, st>>>(p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    ip_nodes_kernel<<<(unsigned)((p.ntot + 255) / 256), 256, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp_combine(int lmax, int64_t nmodes, const double* T, double* out, cudaStream_t st) {
+    ip_combine_kernel<<<512, 256, 0, st>>>(lmax, nmodes, reinterpret_cast<const double2*>(T),
+                                           reinterpret_cast<double2*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace psht

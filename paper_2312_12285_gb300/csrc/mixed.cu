@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
     constexpr int AR = NF == 4 ? 4 : 8;        // A registers per 16-point group
     constexpr int ITEMS = MX_BLK * NV / (MX_WARPS * 32);  // combine items per thread
     constexpr int ARR = MX_P * 4;              // bytes of one array in a tile
-    const int narr = MX_NGEO + p.ncol;
+    const int narr = MX_NGEO + (p.wtab ? 0 : p.ncol);  // table mode: weights come from p.wtab
     const int L = p.lmax;
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -323,8 +323,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     const int q = 32 * k + lane, i = qbase + q;
                     float mant, cs, sn;
                     seed_f32(m, tf[MX_P + i], tf[2 * MX_P + i], lch, lcl, mant, E[k]);
-                    phase_f32(m, tu[3 * MX_P + i], tu[4 * MX_P + i], cs, sn);
-                    my_ph[q] = make_float2(cs, sn);
+                    if (!p.wtab) {
+                        phase_f32(m, tu[3 * MX_P + i], tu[4 * MX_P + i], cs, sn);
+                        my_ph[q] = make_float2(cs, sn);
+                    }
                     const float xv = tf[i];
                     const float na = E[k] == 0 ? -1.f : 0.f;
                     if (k & 1) {
@@ -349,14 +351,22 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
-                        const float2 ph = my_ph[q];
-                        const float trig = comp ? -ph.y : ph.x;
-                        const float wa = fa < p.ncol ? tf[(MX_NGEO + fa) * MX_P + qbase + q] * sca * trig : 0.f;
-                        mx_split_w(wa, ha[e], la[e]);
-                        if (NF == 8) {
-                            const float wb = fb < p.ncol ? tf[(MX_NGEO + fb) * MX_P + qbase + q] * scb * trig : 0.f;
-                            mx_split_w(wb, hb[e], lb[e]);
+                        float wa, wb = 0.f;
+                        if (p.wtab) {
+                            // table mode: W_m[i, f] read as given (complex), scaled per column
+                            const float2* wr =
+                                p.wtab + ((int64_t)m * p.ntot + pt0 + (int64_t)t * MX_P + qbase + q) * p.wtab_ncol;
+                            wa = fa < p.ncol ? (comp ? wr[fa].y : wr[fa].x) * sca : 0.f;
+                            if (NF == 8) wb = fb < p.ncol ? (comp ? wr[fb].y : wr[fb].x) * scb : 0.f;
+                        } else {
+                            const float2 ph = my_ph[q];
+                            const float trig = comp ? -ph.y : ph.x;
+                            wa = fa < p.ncol ? tf[(MX_NGEO + fa) * MX_P + qbase + q] * sca * trig : 0.f;
+                            if (NF == 8)
+                                wb = fb < p.ncol ? tf[(MX_NGEO + fb) * MX_P + qbase + q] * scb * trig : 0.f;
                         }
+                        mx_split_w(wa, ha[e], la[e]);
+                        if (NF == 8) mx_split_w(wb, hb[e], lb[e]);
                     }
                     if (NF == 4) {
                         A[gi][0] = mx_pack(ha[0], ha[1]);

@@ -177,6 +177,35 @@ def alm_columns(plan: Plan, x: torch.Tensor, phi: torch.Tensor, w: torch.Tensor,
     return out
 
 
+def workspace_bytes_interp(plan: Plan, cats, nfield: int, ntheta: int) -> int:
+    arr, n = _lib.catalog_array(_entries(cats, "fp32", plan.device))
+    size = plan.lib.pointsht_workspace_size_interp(plan.handle, arr, n, nfield, int(ntheta))
+    if size == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_interp")
+    return int(size)
+
+
+def default_ntheta(lmax: int) -> int:
+    """16 samples per multipole (relative interpolation error ~1.5e-6), at most 32768."""
+    return min(32768, 16 * lmax)
+
+
+def alm_interp(plan: Plan, cats, nfield: int = 1, ntheta=None, out=None, workspace=None, stream=None):
+    """a_lm of each field by the interpolated route (pointsht_alm_interp):
+    complex128 [nfield, M].  ntheta = samples in theta (None: default_ntheta)."""
+    if ntheta is None:
+        ntheta = default_ntheta(plan.lmax)
+    arr, n = _lib.catalog_array(_entries(cats, "fp32", plan.device))
+    need = workspace_bytes_interp(plan, cats, nfield, ntheta)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=plan.device)
+    if out is None:
+        out = torch.empty((nfield, plan.nmodes), dtype=torch.complex128, device=plan.device)
+    _lib.check(plan.lib.pointsht_alm_interp(plan.handle, arr, n, nfield, int(ntheta), _ptr(out), _ptr(workspace),
+                                            workspace.numel(), _stream_ptr(stream)), "alm_interp")
+    return out
+
+
 def shot_noise_raw(cats, nfield: int, precision: str, device, workspace=None, stream=None, weights=None):
     """Shot-noise matrix [nfield, nfield] (pointsht_shot_noise)."""
     lib = _lib.load()
