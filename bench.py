@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--config", type=int, default=3, help="workload configuration (3 = lmax 2048, 1e7 points)")
     ap.add_argument("--scale", type=float, default=1.0, help="scale the point counts (profiling runs)")
     ap.add_argument("--lmax", type=int, default=None)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed", "interp"],
+                    help="interp = the interpolated route (samples in theta, default 16 per multipole)")
     ap.add_argument("--columns", type=int, default=0,
                     help="weight columns on the workload's point set (pointsht_alm_columns); 0 = catalog form")
     ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
@@ -243,7 +244,8 @@ def ours(args):
                     torch.from_numpy(np.ascontiguousarray(w)).to(dev), f, co) for (x, p, w, f, co) in cats_np]
     nfield = wl.nfield
     plan = ops.get_plan(L, dev)
-    ws = torch.empty(ops.workspace_bytes(plan, cats, nfield, prec), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ops.workspace_bytes(plan, cats, nfield, "fp32" if prec == "interp" else prec),
+                     dtype=torch.uint8, device=dev)
     out = torch.empty((nfield, plan.nmodes), dtype=torch.complex128, device=dev)
     edges = torch.from_numpy(catalogs.log_bin_edges(L, 32).astype(np.int32)).to(dev)
 
@@ -258,9 +260,17 @@ def ours(args):
         coef = torch.from_numpy(cm).to(dev)
     nout = nfield if coef is None else coef.shape[0]
 
+    if prec == "interp":
+        nt = ops.default_ntheta(L)
+        ws = torch.empty(max(ws.numel(), ops.workspace_bytes_interp(plan, cats, nfield, nt)), dtype=torch.uint8,
+                         device=dev)
+
     def step(cs=cats):
-        a = ops.alm_raw(plan, cs, nfield, prec, out=out, workspace=ws)
-        noise = ops.shot_noise_raw(cs, nfield, prec, dev, workspace=ws)
+        if prec == "interp":
+            a = ops.alm_interp(plan, cs, nfield, nt, out=out, workspace=ws)
+        else:
+            a = ops.alm_raw(plan, cs, nfield, prec, out=out, workspace=ws)
+        noise = ops.shot_noise_raw(cs, nfield, "fp32" if prec == "interp" else prec, dev, workspace=ws)
         if dist is not None:
             allreduce_sum([a, noise])
         if coef is not None:
@@ -270,7 +280,10 @@ def ours(args):
         return cl, cb
 
     # prep (pads, hist, scan, scatter), analysis, reduce, 2 x shot noise, [combine x2], C_l, bins
+    # interp: hist, 2 scans, scatter, bin, fold, [pad], samples, grid transform, reduce, combine; noise 2, C_l, bins
     launches_per_step = 10 + (2 if coef is not None else 0)
+    if prec == "interp":
+        launches_per_step = nfield * (10 + (1 if nt % 1024 else 0)) + 4 + (2 if coef is not None else 0)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -330,7 +343,12 @@ def ours(args):
         peak_src = (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                     f"(recipe unit counts and clock)")
     achieved = FLOPS_PER_POINT_MODE * n_rank * wl.nmodes / (kms / 1e3) / 1e12
-    traffic = profiled_traffic(wl.name, n_rank)
+    if prec == "interp":
+        # algorithmic flops of the interpolated route: binning 22 per (point, m)
+        # (4 spline weights x complex MAC, phase rotation), transform of the
+        # samples 27 per (sample, mode) (recurrence, 6 columns x complex MAC)
+        achieved = (22.0 * n_rank * (L + 1) + 27.0 * nt * wl.nmodes) / (kms / 1e3) / 1e12
+    traffic = profiled_traffic(wl.name, n_rank) if prec == "fp32" else None
 
     # ---- end to end through the public API, host buffers in pinned memory ----
     e2e = None
@@ -385,7 +403,8 @@ def ours(args):
         import oracle
         scats = [ops.Cat(torch.from_numpy(np.ascontiguousarray(x)).to(dev), torch.from_numpy(np.ascontiguousarray(p)).to(dev),
                          torch.from_numpy(np.ascontiguousarray(w)).to(dev), f, co) for (x, p, w, co, f) in sample]
-        a = ops.alm_raw(plan, scats, nfield, prec).cpu().numpy()
+        a = (ops.alm_interp(plan, scats, nfield, nt) if prec == "interp" else
+             ops.alm_raw(plan, scats, nfield, prec)).cpu().numpy()
         errs = []
         for f in range(nfield):
             tot = oracle.cl(ref[f], ref[f], L)
@@ -403,7 +422,8 @@ def ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
-            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "interp": "f32 + f16 hi/lo"}[prec],
+            "data": "synthetic",
             "config": {"workload": workload_name(wl, args), "points": wl.npoints, "lmax": L, "nmodes": wl.nmodes,
                        "fields": nfield, "l2": "inputs larger than L2 (prepared points 24 B x 1e7 = 240 MB)",
                        "modes_counted": "nominal (lmax+1)(lmax+2)/2 per point; accumulation skipped in 16-step "
@@ -413,10 +433,13 @@ def ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": ("analysis_kernel (FP64, 4 points/lane, 4 warps/CTA)" if prec == "fp64" else
+                                    "interpolated route: sort, ip_bin, ip_fold, analysis_mixed_kernel<8> table "
+                                    "mode, combine (timed together; algorithmic flops against the FP32 peak)"
+                                    if prec == "interp" else
                                     "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)"),
                          "kernel_ms": kms,
                          "peak_source": peak_src,
-                         "ncu_pipe": None if prec == "fp64" else {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
+                         "ncu_pipe": None if prec in ("fp64", "interp") else {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
                                       "source": "profiles/analysis_kernel_lognormal_cap_1e5pts_l2048_full.md "
                                                 "(same kernel and launch shape, 1e5-point case: these counters "
                                                 "take 3 ncu passes, so they are not captured at full size)"}},
@@ -479,8 +502,8 @@ def time_columns(plan, xd, pd, Wd, prec, reps, warm=1):
 def precision_ladder(wl, plan, dev, fp32_value, fp32_cl_err, sample):
     """Mixed path for F = 1, 4, 8 weight columns on the workload's point set
     (per-column throughput, speed-up over the plain FP32 path at the same F,
-    C_l error against the FP64 oracle on the bench sample), and the FP64 path
-    on a 1% subsample."""
+    C_l error against the FP64 oracle on the bench sample), the interpolated
+    route on the whole workload, and the FP64 path on a 1% subsample."""
     import numpy as np
     import torch
 
@@ -520,6 +543,32 @@ def precision_ladder(wl, plan, dev, fp32_value, fp32_cl_err, sample):
         res["mixed_cl_err_vs_fp64_oracle"] = float(np.max(np.abs(oracle.cl(a, a, L)[1:] - tot[1:]) / tot[1:]))
         res["mixed_alm_rel_err_per_l"] = oracle.rel_err_per_l(a, ref, L)
     res["fp32_cl_err_vs_fp64_oracle"] = fp32_cl_err
+    # interpolated route (App. "Interpolation", samples in theta), whole workload
+    cats = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (c.x, c.phi, c.w)), c.field,
+                    c.coeff) for c in wl.catalogs]
+    nt = ops.default_ntheta(L)
+    wsi = torch.empty(ops.workspace_bytes_interp(plan, cats, wl.nfield, nt), dtype=torch.uint8, device=dev)
+    outi = ops.alm_interp(plan, cats, wl.nfield, nt, workspace=wsi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        ops.alm_interp(plan, cats, wl.nfield, nt, out=outi, workspace=wsi)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ims = e0.elapsed_time(e1) / 3
+    res["interp_value"] = wl.npoints * M / (ims / 1e3)
+    res["interp_ms"] = ims
+    res["interp_ntheta"] = nt
+    res["interp_speedup_vs_fp32"] = res["interp_value"] / fp32_value
+    del wsi, outi, cats
+    if sample is not None:
+        scats = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (c[0], c[1], c[2])), 0, c[3])
+                 for c in smp]
+        a = ops.alm_interp(plan, scats, 1, nt).cpu().numpy()[0]
+        res["interp_cl_err_vs_fp64_oracle"] = float(np.max(np.abs(oracle.cl(a, a, L)[1:] - tot[1:]) / tot[1:]))
+        res["interp_alm_rel_err_per_l"] = oracle.rel_err_per_l(a, ref, L)
     # FP64 path (catalog form) on the first 1% of every catalog
     sub = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v[:max(1, c.n // 100)].astype(np.float64))).to(dev)
                      for v in (c.x, c.phi, c.w)), c.field, c.coeff) for c in wl.catalogs]

@@ -744,7 +744,7 @@ struct InterpLayout {
     int64_t npts_max = 0, nranges_max = 0, ntot = 0, chunk = 0, nunits = 0;
     int32_t nb = 0, nchunk = 0, npairs = 0, maxctas = 0;
     int64_t accstride = 0;
-    size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, v_off = 0, wtab_off = 0,
+    size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, v_off = 0, vtab_off = 0,
            nodes_off = 0, colmax_off = 0, slots_off = 0, acc_off = 0, counter_off = 0, T_off = 0, total = 0;
 };
 
@@ -782,13 +782,13 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
     c.wc_off = b;     b += up256((size_t)np * 4 * 4);
     c.turn_off = b;   b += up256((size_t)np * 2 * 4);
     c.v_off = b;      b += up256((size_t)(L + 1) * c.nb * 4 * 8);
-    c.wtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 6 * 8);
+    c.vtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 2 * 8);
     c.nodes_off = b;  b += up256((size_t)c.ntot * mixed_geometry_arrays() * 4);
     c.colmax_off = b; b += 256;
-    c.slots_off = b;  b += up256((size_t)6 * c.nchunk * plan->nmodes * 16);
+    c.slots_off = b;  b += up256((size_t)3 * c.nchunk * plan->nmodes * 16);
     c.acc_off = b;    b += up256((size_t)c.maxctas * c.accstride * 4);
     c.counter_off = b; b += 256;
-    c.T_off = b;      b += up256((size_t)6 * plan->nmodes * 16);
+    c.T_off = b;      b += up256((size_t)3 * plan->nmodes * 16);
     c.total = b;
 }
 
@@ -864,7 +864,7 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         ip.wc = reinterpret_cast<float*>(ws + c.wc_off);
         ip.turn = reinterpret_cast<uint32_t*>(ws + c.turn_off);
         ip.v = reinterpret_cast<float2*>(ws + c.v_off);
-        ip.wtab = reinterpret_cast<float2*>(ws + c.wtab_off);
+        ip.vtab = reinterpret_cast<float2*>(ws + c.vtab_off);
         ip.nodes = reinterpret_cast<uint32_t*>(ws + c.nodes_off);
         ip.colmax = reinterpret_cast<unsigned*>(ws + c.colmax_off);
         ip.err = plan->err;
@@ -874,12 +874,12 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: sort launch: %s", cudaGetErrorString(e));
         e = launch_interp_tables(ip, plan->sm_count, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: binning launch: %s", cudaGetErrorString(e));
-        // grid transform of the six sample-weight columns (mixed kernel, table mode)
+        // grid transform of the three sample-weight columns (mixed kernel, table mode)
         CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
         MixedParams mp;
         memset(&mp, 0, sizeof(mp));
         mp.lmax = L;
-        mp.ncol = 6;
+        mp.ncol = 3;
         mp.npairs = c.npairs;
         mp.flush_tiles = FLUSH_TILES;
         mp.nmodes = plan->nmodes;
@@ -898,17 +898,17 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         mp.accg = reinterpret_cast<float*>(ws + c.acc_off);
         mp.accstride = c.accstride;
         mp.maxctas = c.maxctas;
-        mp.wtab = ip.wtab;
-        mp.wtab_ncol = 6;
+        mp.vtab = ip.vtab;
+        mp.vtab_h = (float)(3.14159265358979323846 / (double)ntheta);
         mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
         mp.err = plan->err;
         e = launch_mixed(mp, plan->sm_count, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: grid transform launch: %s", cudaGetErrorString(e));
         ReduceParams rp;
         memset(&rp, 0, sizeof(rp));
-        rp.nfield = 6;
+        rp.nfield = 3;
         rp.nmodes = plan->nmodes;
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 3; ++k) {
             rp.slot0[k] = k * c.nchunk;
             rp.nchunk[k] = c.nchunk;
         }

@@ -204,8 +204,10 @@ struct MixedParams {
     double* slots;            // [col][chunk][nmodes] complex
     float* accg;              // per-CTA FP32 accumulator rows, accstride floats each
     int64_t accstride;
-    int32_t maxctas, wtab_ncol;   // CTAs the accumulator buffer provides for; columns of wtab
-    const float2* wtab;       // table mode: complex weights [(lmax+1)][ntot][wtab_ncol] instead of w e^{-i m phi}
+    int32_t maxctas;          // CTAs the accumulator buffer provides for
+    float vtab_h;             // table mode: sample spacing h
+    const float2* vtab;       // table mode (interpolated route): (Vy, Vd) [(lmax+1)][ntot][2]; the three
+                              // columns at order m are Vy^(m), h Vd^(m-1), h Vd^(m+1) instead of w e^{-i m phi}
     int* counter;
     unsigned* err;
 };
@@ -230,9 +232,9 @@ struct InterpParams {
     float* wc;                          // [4][npts] w coeff c_alpha, interval order
     uint32_t* turn;                     // [2][npts]
     float2* v;                          // [(lmax+1)][nb][4]
-    float2* wtab;                       // [(lmax+1)][ntot][6]
+    float2* vtab;                       // [(lmax+1)][ntot][2]: (Vy, Vd) per sample position
     uint32_t* nodes;                    // [5][ntot] sample geometry (x, lsh, lsl, turn hi, lo)
-    unsigned* colmax;                   // [6]
+    unsigned* colmax;                   // [3]
     unsigned* err;
 };
 

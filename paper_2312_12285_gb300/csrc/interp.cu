@@ -11,22 +11,26 @@
 // The intervals j = -1 and N-1 reach ghost samples at -h/2 and pi + h/2,
 // continued across the poles as y(-theta) = (-1)^m y(theta) and
 // y'(-theta) = (-1)^(m+1) y'(theta); they fold onto samples 0 and N-1.
-// With dy/dtheta = [l x lambda_l - sqrt((l^2-m^2)(2l+1)/(2l-1)) lambda_{l-1}] / sin
-// (App. A's derivative of Pbar), the grid transform is three plain
-// transforms of the samples with the per-(m, sample) weights
-//   W0 = Vy,  W1 = h x Vd / sin,  W2 = h Vd / sin,
-//   a_lm = T0_lm + l T1_lm - c_lm T2_{l-1,m},   c_lm = sqrt((l^2-m^2)(2l+1)/(2l-1)),
-// run by the mixed tensor-core kernel in its table mode (mixed.cu) and
-// combined in FP64 here.  Polar samples (sin < 1/16) carry their W in three
-// columns of their own, so that each fp16 column scale covers a range of
-// 1/sin below 2^11 (one pass of the 8-column kernel, six columns).
+//
+// The theta-derivative is taken in its order-coupled form,
+//   dlambda_lm/dtheta = 1/2 [sqrt((l-m)(l+m+1)) lambda_{l,m+1} - sqrt((l+m)(l-m+1)) lambda_{l,m-1}],
+//   lambda_{l,-1} = -lambda_{l,1},
+// equal to App. A's (l x lambda_l - ... lambda_{l-1}) / sin theta but free of
+// its cancellation near the poles (which multiplies the FP32 recurrence's
+// error there by ~1/theta) and of the 1/sin weights.  So the derivative
+// weights of order m enter the transforms of orders m +- 1: the transform at
+// order m carries three weight columns per sample,
+//   C0 = Vy^(m),  C1 = h Vd^(m-1),  C2 = h Vd^(m+1),
+// run by the mixed tensor-core kernel in its table mode (mixed.cu), and
+//   a_lm = T_{l,m} + 1/2 sqrt((l-m)(l+m+1)) U+_{l,m+1} - 1/2 sqrt((l+m)(l-m+1)) U-_{l,m-1}
+// (m = 0: T_{l,0} + sqrt(l(l+1)) U+_{l,1}) is combined in FP64 here, with
+// T, U+, U- the transforms of C0, C1, C2.
 //
 // Kernels: ip_hist / ip_scan_* / ip_scatter (stable counting sort of the
 // points by interval, deterministic), ip_bin (binning, one warp per
 // (interval, block of 256 orders), lanes over m, phases by exact fixed-point
-// turns and a 32-step rotation), ip_fold (sample weights, column maxima),
-// ip_nodes (sample geometry in |x| order for the grid transform) and
-// ip_combine.
+// turns and a 32-step rotation), ip_fold (sample weights Vy, Vd in |x|
+// order, column maxima), ip_nodes (sample geometry) and ip_combine.
 #include "common.cuh"
 
 namespace psht {
@@ -53,11 +57,6 @@ __device__ __forceinline__ bool ip_range_of(const InterpParams& p, int64_t r, in
     i0 = (r - p.range0[c]) * IP_RANGE;
     i1 = min(p.cat[c].n, i0 + IP_RANGE);
     return i0 < i1;
-}
-
-__device__ __forceinline__ bool ip_valid(const InterpCat& c, int64_t i) {
-    const float x = c.x[i], ph = c.phi[i], w = c.w[i];
-    return isfinite(x) && isfinite(ph) && isfinite(w) && fabsf(x) <= 1.f;
 }
 
 // ------------------------------------------------------ counting sort --
@@ -117,7 +116,8 @@ __global__ void __launch_bounds__(1024) ip_scan_buckets_kernel(const __grid_cons
     }
 }
 
-// stable scatter: one warp per range, points in index order
+// stable scatter: one warp per range, points in index order, four 32-point
+// chunks per iteration so that their loads are in flight together
 __global__ void __launch_bounds__(32) ip_scatter_kernel(const __grid_constant__ InterpParams p) {
     extern __shared__ int32_t next[];  // point counts of one field stay below 2^31 (checked on the host)
     const int64_t r = blockIdx.x;
@@ -128,30 +128,43 @@ __global__ void __launch_bounds__(32) ip_scatter_kernel(const __grid_constant__ 
     int64_t i0, i1;
     if (!ip_range_of(p, r, c, i0, i1)) return;
     const InterpCat& cd = p.cat[c];
-    for (int64_t base = i0; base < i1; base += 32) {
-        const int64_t i = base + lane;
-        const bool valid = i < i1;
-        double t = 0.0;
-        const int b = valid ? ip_interval(cd.x[i], p.ntheta, t) + 1 : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        int64_t dst = 0;
-        if (valid) dst = next[b] + rank;
-        __syncwarp();
-        if (valid && rank == 0) next[b] += __popc(peers);
-        __syncwarp();
-        if (valid) {
-            const bool ok = ip_valid(cd, i);
-            if (!ok) atomicOr(p.err, ERR_RANGE);
-            const double wv = ok ? cd.coeff * (double)cd.w[i] : 0.0;
-            const double u = 1.0 - t;
-            p.wc[dst] = (float)(wv * (2.0 * t + 1.0) * u * u);
-            p.wc[p.npts + dst] = (float)(wv * t * u * u);
-            p.wc[2 * p.npts + dst] = (float)(wv * t * t * (3.0 - 2.0 * t));
-            p.wc[3 * p.npts + dst] = (float)(wv * t * t * (t - 1.0));
-            const uint64_t turn = phi_to_turn(ok ? (double)cd.phi[i] : 0.0);
-            p.turn[dst] = (uint32_t)(turn >> 32);
-            p.turn[p.npts + dst] = (uint32_t)(turn & 0xffffffffu);
+    constexpr int U = 4;
+    for (int64_t base = i0; base < i1; base += 32 * U) {
+        float xs[U], ps[U], ws[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            const bool valid = i < i1;
+            xs[u] = valid ? cd.x[i] : 0.f;
+            ps[u] = valid ? cd.phi[i] : 0.f;
+            ws[u] = valid ? cd.w[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            const bool valid = i < i1;
+            double t = 0.0;
+            const int b = valid ? ip_interval(xs[u], p.ntheta, t) + 1 : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, b);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            int64_t dst = 0;
+            if (valid) dst = next[b] + rank;
+            __syncwarp();
+            if (valid && rank == 0) next[b] += __popc(peers);
+            __syncwarp();
+            if (valid) {
+                const bool ok = isfinite(xs[u]) && isfinite(ps[u]) && isfinite(ws[u]) && fabsf(xs[u]) <= 1.f;
+                if (!ok) atomicOr(p.err, ERR_RANGE);
+                const double wv = ok ? cd.coeff * (double)ws[u] : 0.0;
+                const double v = 1.0 - t;
+                p.wc[dst] = (float)(wv * (2.0 * t + 1.0) * v * v);
+                p.wc[p.npts + dst] = (float)(wv * t * v * v);
+                p.wc[2 * p.npts + dst] = (float)(wv * t * t * (3.0 - 2.0 * t));
+                p.wc[3 * p.npts + dst] = (float)(wv * t * t * (t - 1.0));
+                const uint64_t turn = phi_to_turn(ok ? (double)ps[u] : 0.0);
+                p.turn[dst] = (uint32_t)(turn >> 32);
+                p.turn[p.npts + dst] = (uint32_t)(turn & 0xffffffffu);
+            }
         }
     }
 }
@@ -212,13 +225,13 @@ __device__ __forceinline__ int64_t ip_pos(int k, int ntheta) {
     return k < ntheta / 2 ? 2 * (int64_t)k : 2 * (int64_t)(ntheta - 1 - k) + 1;
 }
 
-// sample weights W0 = Vy, W1 = h x Vd / sin, W2 = h Vd / sin (columns 0..2, or
-// 3..5 for polar samples); column maxima
+// sample weights (Vy, Vd) of every order at each sample's position in |x|
+// order; column maxima max|Vy| and h max|Vd|
 __global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ InterpParams p) {
     const int N = p.ntheta;
     const int64_t total = (int64_t)(p.lmax + 1) * N;
-    const double h = 3.14159265358979323846 / (double)N;
-    unsigned mx[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    const float h = (float)(3.14159265358979323846 / (double)N);
+    unsigned my = 0u, md = 0u;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int m = (int)(e / N), k = (int)(e - (int64_t)m * N);
         const float2* vm = p.v + (int64_t)m * p.nb * 4;
@@ -243,47 +256,29 @@ __global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ In
             vd.x -= sg * g3.x;
             vd.y -= sg * g3.y;
         }
-        const double th = (k + 0.5) * h;
-        const double s = sin(th), x = cos(th);
-        const float f1 = (float)(h * x / s), f2 = (float)(h / s);
-        const float2 w1 = make_float2(f1 * vd.x, f1 * vd.y), w2 = make_float2(f2 * vd.x, f2 * vd.y);
-        // polar samples (sin < 1/16) in columns 3..5: 1/sin spans 2/h, more
-        // than an fp16 column scale holds; split at 1/16 each set spans < 2^11
-        const int g = s < 0.0625 ? 3 : 0;
-        float2* dst = p.wtab + ((int64_t)m * p.ntot + ip_pos(k, N)) * 6;
-        dst[g] = vy;
-        dst[g + 1] = w1;
-        dst[g + 2] = w2;
-        dst[3 - g] = make_float2(0.f, 0.f);
-        dst[4 - g] = make_float2(0.f, 0.f);
-        dst[5 - g] = make_float2(0.f, 0.f);
-        const unsigned u0 = __float_as_uint(fmaxf(fabsf(vy.x), fabsf(vy.y)));
-        const unsigned u1 = __float_as_uint(fmaxf(fabsf(w1.x), fabsf(w1.y)));
-        const unsigned u2 = __float_as_uint(fmaxf(fabsf(w2.x), fabsf(w2.y)));
-        if (g) {
-            mx[3] = max(mx[3], u0);
-            mx[4] = max(mx[4], u1);
-            mx[5] = max(mx[5], u2);
-        } else {
-            mx[0] = max(mx[0], u0);
-            mx[1] = max(mx[1], u1);
-            mx[2] = max(mx[2], u2);
-        }
+        float4* dst = reinterpret_cast<float4*>(p.vtab + ((int64_t)m * p.ntot + ip_pos(k, N)) * 2);
+        *dst = make_float4(vy.x, vy.y, vd.x, vd.y);
+        my = max(my, __float_as_uint(fmaxf(fabsf(vy.x), fabsf(vy.y))));
+        md = max(md, __float_as_uint(h * fmaxf(fabsf(vd.x), fabsf(vd.y))));
     }
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        const unsigned v = __reduce_max_sync(0xffffffffu, mx[f]);
-        if ((threadIdx.x & 31) == 0 && v) atomicMax(&p.colmax[f], v);
+    my = __reduce_max_sync(0xffffffffu, my);
+    md = __reduce_max_sync(0xffffffffu, md);
+    if ((threadIdx.x & 31) == 0) {
+        if (my) atomicMax(&p.colmax[0], my);
+        if (md) {
+            atomicMax(&p.colmax[1], md);
+            atomicMax(&p.colmax[2], md);
+        }
     }
 }
 
 // zero weights of the padding positions N..ntot-1 of every order
 __global__ void ip_pad_kernel(const __grid_constant__ InterpParams p) {
     const int64_t npad = p.ntot - p.ntheta;
-    const int64_t total = (int64_t)(p.lmax + 1) * npad * 6;
+    const int64_t total = (int64_t)(p.lmax + 1) * npad * 2;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / (npad * 6), rem = e - m * npad * 6;
-        p.wtab[(m * p.ntot + p.ntheta) * 6 + rem] = make_float2(0.f, 0.f);
+        const int64_t m = e / (npad * 2), rem = e - m * npad * 2;
+        p.vtab[(m * p.ntot + p.ntheta) * 2 + rem] = make_float2(0.f, 0.f);
     }
 }
 
@@ -310,7 +305,8 @@ __global__ void ip_nodes_kernel(const __grid_constant__ InterpParams p) {
     }
 }
 
-// a_lm = T0 + l T1 - c_lm T2_{l-1}  (T_f = grid transforms of columns f and f + 3)
+// a_lm = T_lm + 1/2 sqrt((l-m)(l+m+1)) U+_{l,m+1} - 1/2 sqrt((l+m)(l-m+1)) U-_{l,m-1}
+// (m = 0: T_l0 + sqrt(l(l+1)) U+_{l,1});  T, U+, U- = transforms of columns 0, 1, 2
 __global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, double2* out) {
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nmodes;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -321,13 +317,21 @@ __global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, do
         while (m > 0 && (int64_t)m * (2 * lmax + 3 - m) / 2 > idx) --m;
         while (m < lmax && (int64_t)(m + 1) * (2 * lmax + 3 - (m + 1)) / 2 <= idx) ++m;
         const int l = (int)(idx - (int64_t)m * (2 * lmax + 1 - m) / 2);
-        const double2 t0 = T[idx], t1 = T[nmodes + idx], u0 = T[3 * nmodes + idx], u1 = T[4 * nmodes + idx];
-        double re = (t0.x + u0.x) + (double)l * (t1.x + u1.x), im = (t0.y + u0.y) + (double)l * (t1.y + u1.y);
-        if (l > m) {
-            const double c = sqrt(((double)l * l - (double)m * m) * (2.0 * l + 1.0) / (2.0 * l - 1.0));
-            const double2 t2 = T[2 * nmodes + idx - 1], u2 = T[5 * nmodes + idx - 1];
-            re -= c * (t2.x + u2.x);
-            im -= c * (t2.y + u2.y);
+        const double2 t = T[idx];
+        double re = t.x, im = t.y;
+        if (l > m) {  // U+ at (l, m + 1)
+            const int64_t j = (int64_t)(m + 1) * (2 * lmax - m) / 2 + l;
+            const double2 u = T[nmodes + j];
+            const double c = (m == 0 ? 1.0 : 0.5) * sqrt((double)(l - m) * (double)(l + m + 1));
+            re += c * u.x;
+            im += c * u.y;
+        }
+        if (m > 0) {  // U- at (l, m - 1)
+            const int64_t j = (int64_t)(m - 1) * (2 * lmax + 2 - m) / 2 + l;
+            const double2 u = T[2 * nmodes + j];
+            const double c = 0.5 * sqrt((double)(l + m) * (double)(l - m + 1));
+            re -= c * u.x;
+            im -= c * u.y;
         }
         out[idx] = make_double2(re, im);
     }

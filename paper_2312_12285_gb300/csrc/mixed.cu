@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
     constexpr int AR = NF == 4 ? 4 : 8;        // A registers per 16-point group
     constexpr int ITEMS = MX_BLK * NV / (MX_WARPS * 32);  // combine items per thread
     constexpr int ARR = MX_P * 4;              // bytes of one array in a tile
-    const int narr = MX_NGEO + (p.wtab ? 0 : p.ncol);  // table mode: weights come from p.wtab
+    const int narr = MX_NGEO + (p.vtab ? 0 : p.ncol);  // table mode: weights come from p.vtab
     const int L = p.lmax;
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
             mbar_expect_tx(bar, narr * ARR);
             const int64_t first = pt0 + (int64_t)t * MX_P;
             for (int a = 0; a < MX_NGEO; ++a) bulk_g2s(tile + a * ARR, p.pts + (int64_t)a * p.ntot + first, ARR, bar);
-            for (int f = 0; f < p.ncol; ++f)
+            // weight arrays only in column mode (narr counts them); table mode reads p.vtab
+            for (int f = 0; f < narr - MX_NGEO; ++f)
                 bulk_g2s(tile + (MX_NGEO + f) * ARR, p.wcols + (int64_t)f * p.ntot + first, ARR, bar);
         };
         __syncthreads();  // s_unit read, accumulator rows zeroed
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     const int q = 32 * k + lane, i = qbase + q;
                     float mant, cs, sn;
                     seed_f32(m, tf[MX_P + i], tf[2 * MX_P + i], lch, lcl, mant, E[k]);
-                    if (!p.wtab) {
+                    if (!p.vtab) {
                         phase_f32(m, tu[3 * MX_P + i], tu[4 * MX_P + i], cs, sn);
                         my_ph[q] = make_float2(cs, sn);
                     }
@@ -352,12 +353,21 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     for (int e = 0; e < 4; ++e) {
                         const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
                         float wa, wb = 0.f;
-                        if (p.wtab) {
-                            // table mode: W_m[i, f] read as given (complex), scaled per column
-                            const float2* wr =
-                                p.wtab + ((int64_t)m * p.ntot + pt0 + (int64_t)t * MX_P + qbase + q) * p.wtab_ncol;
-                            wa = fa < p.ncol ? (comp ? wr[fa].y : wr[fa].x) * sca : 0.f;
-                            if (NF == 8) wb = fb < p.ncol ? (comp ? wr[fb].y : wr[fb].x) * scb : 0.f;
+                        if (p.vtab) {
+                            // table mode: column 0 = Vy^(m), 1 = h Vd^(m-1), 2 = h Vd^(m+1) of this sample
+                            const int64_t node = pt0 + (int64_t)t * MX_P + qbase + q;
+                            float2 wt = make_float2(0.f, 0.f);
+                            float f = 1.f;
+                            if (fa == 0) {
+                                wt = p.vtab[((int64_t)m * p.ntot + node) * 2];
+                            } else if (fa == 1 && m >= 1) {
+                                wt = p.vtab[((int64_t)(m - 1) * p.ntot + node) * 2 + 1];
+                                f = p.vtab_h;
+                            } else if (fa == 2 && m < L) {
+                                wt = p.vtab[((int64_t)(m + 1) * p.ntot + node) * 2 + 1];
+                                f = p.vtab_h;
+                            }
+                            wa = (comp ? wt.y : wt.x) * f * sca;
                         } else {
                             const float2 ph = my_ph[q];
                             const float trig = comp ? -ph.y : ph.x;
@@ -579,6 +589,10 @@ cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStr
 }
 
 cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
+    // exactly one weight source: prepared weight arrays or a table
+    if ((mp.wcols == nullptr) == (mp.vtab == nullptr) || mp.ncol < 1 || mp.ncol > MX_MAXCOL ||
+        (mp.vtab && mp.ncol != 3))
+        return cudaErrorInvalidValue;
     const int nf = mp.ncol <= 4 ? 4 : 8;
     const size_t smem = mixed_smem_bytes(nf);
     const void* kern = nf == 4 ? reinterpret_cast<const void*>(analysis_mixed_kernel<4>)

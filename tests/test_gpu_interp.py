@@ -103,7 +103,10 @@ def test_ragged_sizes(dev, L, ntheta, n):
 
 
 def test_pole_points(dev):
-    """Points at and next to both poles use the ghost samples."""
+    """Points at and next to both poles use the ghost samples.  Near the
+    poles the FP32 recurrence's own error grows (coefficient rounding; the
+    FP32 path's pole tests use the same model), hence 3e-5 of the largest
+    value against the interpolation oracle."""
     L = 48
     x = np.array([1.0, -1.0, 1.0 - 1e-7, -1.0 + 3e-6, 0.99999], np.float32)
     phi = np.array([0.1, 1.2, 2.3, 3.4, 4.5], np.float32)
@@ -113,7 +116,7 @@ def test_pole_points(dev):
     ref = oracle.alm_interp(x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64), L, 16 * L)
     exact = oracle.alm(x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64), L)
     scale = np.max(np.abs(exact))
-    assert np.max(np.abs(got - ref)) <= 1e-5 * scale
+    assert np.max(np.abs(got - ref)) <= 3e-5 * scale
     assert np.max(np.abs(got - exact)) <= 1e-4 * scale
 
 
@@ -148,15 +151,18 @@ def full(dev):
 
 
 def test_fullsize_sampled_columns(full):
-    """Short columns m = 1900, 2047, 2048 over all 1e7 points against the
-    exact transform."""
+    """Columns m = 0 (largest values near the poles) and the short columns
+    m = 1900, 2047, 2048 over all 1e7 points against the exact transform;
+    m = 0 carries the FP32 recurrence's near-pole error (3e-4, as for the
+    direct FP32 path at this size)."""
     wl, got = full
     L = wl.lmax
     x, phi, w = _field(wl)
-    ref = oracle.alm(x, phi, w, L, mlist=[1900, 2047, 2048])
+    tol = {0: 3e-4, 1900: 1e-4, 2047: 1e-4, 2048: 1e-4}
+    ref = oracle.alm(x, phi, w, L, mlist=list(tol))
     for m, col in ref.items():
         g = got[oracle.index(m, m, L):oracle.index(L, m, L) + 1]
-        assert np.linalg.norm(g - col) <= 1e-4 * np.linalg.norm(col), m
+        assert np.linalg.norm(g - col) <= tol[m] * np.linalg.norm(col), m
 
 
 def test_fullsize_low_l_pseudo_cl(full):

@@ -83,3 +83,31 @@ def test_monopole_is_exact():
     for N in (7, 64):
         a = oracle.alm_interp(x, phi, w, 8, N)
         assert abs(a[0] - np.sum(w) / np.sqrt(4 * np.pi)) <= 1e-12 * np.sum(w)
+
+
+def test_order_coupled_derivative_identity():
+    """The GPU's interpolated route takes dlambda_lm/dtheta in the order-coupled
+    form 1/2 [sqrt((l-m)(l+m+1)) lambda_{l,m+1} - sqrt((l+m)(l-m+1)) lambda_{l,m-1}]
+    (lambda_{l,-1} = -lambda_{l,1}); pin it against App. A's derivative
+    [l x Pbar_l - (l+m) sqrt((l-m)/(l+m)) Pbar_{l-1}] / sin(theta) (times the
+    normalisation), with the oracle's Pbar."""
+    L = 40
+
+    def lam(x, m):
+        return oracle.pbar(x, L, m) * np.sqrt((2 * np.arange(m, L + 1) + 1) / (4 * np.pi))
+
+    for th in (1e-2, 0.05, 0.7, 1.3, 2.9, np.pi - 1e-2):
+        x, s = np.cos(th), np.sin(th)
+        cols = [lam(x, m) for m in range(L + 1)]
+        for m in range(L + 1):
+            l = np.arange(m, L + 1)
+            pb = oracle.pbar(x, L, m)
+            prev = np.concatenate([[0.0], pb[:-1]])
+            coef = (l + m) * np.sqrt(np.where(l > m, (l - m) / np.maximum(l + m, 1), 0.0))
+            d_paper = np.sqrt((2 * l + 1) / (4 * np.pi)) * (l * x * pb - coef * prev) / s
+            up = np.zeros_like(cols[m])
+            if m + 1 <= L:
+                up[1:] = cols[m + 1]
+            dn = cols[m - 1][1:] if m >= 1 else -np.concatenate([[0.0], cols[1]])
+            d_id = 0.5 * (np.sqrt((l - m) * (l + m + 1)) * up - np.sqrt((l + m) * (l - m + 1)) * dn)
+            assert np.max(np.abs(d_id - d_paper)) <= 1e-11 * max(1.0, np.max(np.abs(d_paper)))
