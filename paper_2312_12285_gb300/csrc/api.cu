@@ -763,7 +763,7 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
         c.nranges_max = std::max(c.nranges_max, nr);
     }
     c.nb = ntheta + 1;
-    c.ntot = ((int64_t)ntheta + P - 1) / P * P;
+    c.ntot = ((int64_t)ntheta / 2 + P - 1) / P * P;  // positions: north samples, the south ones mirrored
     c.npairs = L / 2 + 1;
     const int64_t target = (int64_t)4 * plan->sm_count;
     int64_t chunk = P;
@@ -782,13 +782,13 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
     c.wc_off = b;     b += up256((size_t)np * 4 * 4);
     c.turn_off = b;   b += up256((size_t)np * 2 * 4);
     c.v_off = b;      b += up256((size_t)(L + 1) * c.nb * 4 * 8);
-    c.vtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 2 * 8);
+    c.vtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 4 * 8);
     c.nodes_off = b;  b += up256((size_t)c.ntot * mixed_geometry_arrays() * 4);
     c.colmax_off = b; b += 256;
-    c.slots_off = b;  b += up256((size_t)3 * c.nchunk * plan->nmodes * 16);
+    c.slots_off = b;  b += up256((size_t)6 * c.nchunk * plan->nmodes * 16);
     c.acc_off = b;    b += up256((size_t)c.maxctas * c.accstride * 4);
     c.counter_off = b; b += 256;
-    c.T_off = b;      b += up256((size_t)3 * plan->nmodes * 16);
+    c.T_off = b;      b += up256((size_t)6 * plan->nmodes * 16);
     c.total = b;
 }
 
@@ -874,12 +874,12 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: sort launch: %s", cudaGetErrorString(e));
         e = launch_interp_tables(ip, plan->sm_count, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: binning launch: %s", cudaGetErrorString(e));
-        // grid transform of the three sample-weight columns (mixed kernel, table mode)
+        // transform of the six sample-weight columns (mixed kernel, table mode)
         CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
         MixedParams mp;
         memset(&mp, 0, sizeof(mp));
         mp.lmax = L;
-        mp.ncol = 3;
+        mp.ncol = 6;
         mp.npairs = c.npairs;
         mp.flush_tiles = FLUSH_TILES;
         mp.nmodes = plan->nmodes;
@@ -906,9 +906,9 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: grid transform launch: %s", cudaGetErrorString(e));
         ReduceParams rp;
         memset(&rp, 0, sizeof(rp));
-        rp.nfield = 3;
+        rp.nfield = 6;
         rp.nmodes = plan->nmodes;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 6; ++k) {
             rp.slot0[k] = k * c.nchunk;
             rp.nchunk[k] = c.nchunk;
         }

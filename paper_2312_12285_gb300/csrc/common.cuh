@@ -206,8 +206,9 @@ struct MixedParams {
     int64_t accstride;
     int32_t maxctas;          // CTAs the accumulator buffer provides for
     float vtab_h;             // table mode: sample spacing h
-    const float2* vtab;       // table mode (interpolated route): (Vy, Vd) [(lmax+1)][ntot][2]; the three
-                              // columns at order m are Vy^(m), h Vd^(m-1), h Vd^(m+1) instead of w e^{-i m phi}
+    const float2* vtab;       // table mode (interpolated route): [(lmax+1)][ntot][4] = (Vy, Vd) of the north
+                              // and the mirrored south sample at each position; the six columns at order m
+                              // are Vy^(m), h Vd^(m-1), h Vd^(m+1) of each instead of w e^{-i m phi}
     int* counter;
     unsigned* err;
 };
@@ -232,9 +233,9 @@ struct InterpParams {
     float* wc;                          // [4][npts] w coeff c_alpha, interval order
     uint32_t* turn;                     // [2][npts]
     float2* v;                          // [(lmax+1)][nb][4]
-    float2* vtab;                       // [(lmax+1)][ntot][2]: (Vy, Vd) per sample position
+    float2* vtab;                       // [(lmax+1)][ntot][4]: (Vy, Vd) north, (Vy, Vd) south per position
     uint32_t* nodes;                    // [5][ntot] sample geometry (x, lsh, lsl, turn hi, lo)
-    unsigned* colmax;                   // [3]
+    unsigned* colmax;                   // [6]
     unsigned* err;
 };
 

@@ -26,6 +26,12 @@
 // (m = 0: T_{l,0} + sqrt(l(l+1)) U+_{l,1}) is combined in FP64 here, with
 // T, U+, U- the transforms of C0, C1, C2.
 //
+// A south sample s_{N-1-k} = pi - s_k has |x| and sin of s_k, and
+// lambda_lm(-x) = (-1)^(l+m) lambda_lm(x): both share one position of the
+// transform (north weights in columns 0..2, south in 3..5), and the parity
+// is applied in the combination.  Positions carry u = x - 1 = -2 sin^2(s/2),
+// exact to FP32 relative precision next to the pole.
+//
 // Kernels: ip_hist / ip_scan_* / ip_scatter (stable counting sort of the
 // points by interval, deterministic), ip_bin (binning, one warp per
 // (interval, block of 256 orders), lanes over m, phases by exact fixed-point
@@ -220,13 +226,8 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
     }
 }
 
-// sample k -> position in the grid transform (|x| descending: both poles first)
-__device__ __forceinline__ int64_t ip_pos(int k, int ntheta) {
-    return k < ntheta / 2 ? 2 * (int64_t)k : 2 * (int64_t)(ntheta - 1 - k) + 1;
-}
-
-// sample weights (Vy, Vd) of every order at each sample's position in |x|
-// order; column maxima max|Vy| and h max|Vd|
+// sample weights (Vy, Vd) of every order at each sample's position (north
+// and mirrored south halves); column maxima max|Vy| and h max|Vd|
 __global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ InterpParams p) {
     const int N = p.ntheta;
     const int64_t total = (int64_t)(p.lmax + 1) * N;
@@ -256,7 +257,10 @@ __global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ In
             vd.x -= sg * g3.x;
             vd.y -= sg * g3.y;
         }
-        float4* dst = reinterpret_cast<float4*>(p.vtab + ((int64_t)m * p.ntot + ip_pos(k, N)) * 2);
+        // north sample k at position k, south sample N-1-k at the same position
+        const int half = k >= N / 2;
+        const int64_t pos = half ? N - 1 - k : k;
+        float4* dst = reinterpret_cast<float4*>(p.vtab + ((int64_t)m * p.ntot + pos) * 4 + 2 * half);
         *dst = make_float4(vy.x, vy.y, vd.x, vd.y);
         my = max(my, __float_as_uint(fmaxf(fabsf(vy.x), fabsf(vy.y))));
         md = max(md, __float_as_uint(h * fmaxf(fabsf(vd.x), fabsf(vd.y))));
@@ -264,35 +268,41 @@ __global__ void __launch_bounds__(256) ip_fold_kernel(const __grid_constant__ In
     my = __reduce_max_sync(0xffffffffu, my);
     md = __reduce_max_sync(0xffffffffu, md);
     if ((threadIdx.x & 31) == 0) {
-        if (my) atomicMax(&p.colmax[0], my);
+        if (my) {
+            atomicMax(&p.colmax[0], my);
+            atomicMax(&p.colmax[3], my);
+        }
         if (md) {
             atomicMax(&p.colmax[1], md);
             atomicMax(&p.colmax[2], md);
+            atomicMax(&p.colmax[4], md);
+            atomicMax(&p.colmax[5], md);
         }
     }
 }
 
 // zero weights of the padding positions N..ntot-1 of every order
 __global__ void ip_pad_kernel(const __grid_constant__ InterpParams p) {
-    const int64_t npad = p.ntot - p.ntheta;
-    const int64_t total = (int64_t)(p.lmax + 1) * npad * 2;
+    const int64_t half = p.ntheta / 2, npad = p.ntot - half;
+    const int64_t total = (int64_t)(p.lmax + 1) * npad * 4;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / (npad * 2), rem = e - m * npad * 2;
-        p.vtab[(m * p.ntot + p.ntheta) * 2 + rem] = make_float2(0.f, 0.f);
+        const int64_t m = e / (npad * 4), rem = e - m * npad * 4;
+        p.vtab[(m * p.ntot + half) * 4 + rem] = make_float2(0.f, 0.f);
     }
 }
 
-// sample geometry in the layout of the mixed kernel (x, log2 sin hi/lo, turn 0)
+// geometry of the positions in the layout of the mixed kernel: u = x - 1 of
+// the north sample (= -2 sin^2(s/2)), log2 sin hi/lo, turn 0; padding at x = 0
 __global__ void ip_nodes_kernel(const __grid_constant__ InterpParams p) {
     const int N = p.ntheta;
     const double h = 3.14159265358979323846 / (double)N;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < p.ntot; q += (int64_t)gridDim.x * blockDim.x) {
-        float x = 0.f, lh = 0.f, ll = 0.f;
-        if (q < N) {
-            const int k = (q & 1) ? N - 1 - (int)(q >> 1) : (int)(q >> 1);
-            const double th = (k + 0.5) * h;
+        float x = -1.f, lh = 0.f, ll = 0.f;
+        if (q < N / 2) {
+            const double th = (q + 0.5) * h;
+            const double sh = sin(0.5 * th);
             const double ls = log2(sin(th));
-            x = (float)cos(th);
+            x = (float)(-2.0 * sh * sh);
             lh = (float)ls;
             ll = (float)(ls - (double)lh);
         }
@@ -307,6 +317,7 @@ __global__ void ip_nodes_kernel(const __grid_constant__ InterpParams p) {
 
 // a_lm = T_lm + 1/2 sqrt((l-m)(l+m+1)) U+_{l,m+1} - 1/2 sqrt((l+m)(l-m+1)) U-_{l,m-1}
 // (m = 0: T_l0 + sqrt(l(l+1)) U+_{l,1});  T, U+, U- = transforms of columns 0, 1, 2
+// (north) and 3, 4, 5 (south)
 __global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, double2* out) {
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nmodes;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -317,18 +328,24 @@ __global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, do
         while (m > 0 && (int64_t)m * (2 * lmax + 3 - m) / 2 > idx) --m;
         while (m < lmax && (int64_t)(m + 1) * (2 * lmax + 3 - (m + 1)) / 2 <= idx) ++m;
         const int l = (int)(idx - (int64_t)m * (2 * lmax + 1 - m) / 2);
-        const double2 t = T[idx];
+        // transform f at (l, mm): north part + (-1)^(l+mm) south part
+        auto X = [&](int f, int mm, int64_t j) {
+            const double2 a = T[f * nmodes + j], b = T[(f + 3) * nmodes + j];
+            const double sg = ((l + mm) & 1) ? -1.0 : 1.0;
+            return make_double2(a.x + sg * b.x, a.y + sg * b.y);
+        };
+        const double2 t = X(0, m, idx);
         double re = t.x, im = t.y;
         if (l > m) {  // U+ at (l, m + 1)
             const int64_t j = (int64_t)(m + 1) * (2 * lmax - m) / 2 + l;
-            const double2 u = T[nmodes + j];
+            const double2 u = X(1, m + 1, j);
             const double c = (m == 0 ? 1.0 : 0.5) * sqrt((double)(l - m) * (double)(l + m + 1));
             re += c * u.x;
             im += c * u.y;
         }
         if (m > 0) {  // U- at (l, m - 1)
             const int64_t j = (int64_t)(m - 1) * (2 * lmax + 2 - m) / 2 + l;
-            const double2 u = T[2 * nmodes + j];
+            const double2 u = X(2, m - 1, j);
             const double c = 0.5 * sqrt((double)(l + m) * (double)(l - m + 1));
             re -= c * u.x;
             im -= c * u.y;
@@ -368,7 +385,7 @@ cudaError_t launch_interp_tables(const InterpParams& p, int sm_count, cudaStream
     if (e != cudaSuccess) return e;
     ip_fold_kernel<<<sm_count * 8, 256, 0, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (p.ntot > p.ntheta) {
+    if (p.ntot > p.ntheta / 2) {
         ip_pad_kernel<<<sm_count * 4, 256, 0, st>>>(p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -62,7 +62,7 @@ __device__ __forceinline__ void mx_write(const PrepColsParams& p, int64_t j, flo
     const uint64_t turn = phi_to_turn((double)ph);
     float* b = reinterpret_cast<float*>(p.pts);
     const float lh = (float)ls;
-    b[j] = x;
+    b[j] = x - 1.f;  // u = x - 1 (exact for x >= 1/2)
     b[p.ntot + j] = lh;
     b[2 * p.ntot + j] = (float)(ls - (double)lh);
     p.pts[3 * p.ntot + j] = (uint32_t)(turn >> 32);
@@ -128,13 +128,6 @@ __device__ __forceinline__ float2 mx_fma2(float2 a, float2 b, float2 c) {
           "l"(reinterpret_cast<unsigned long long&>(c)));
     return d;
 }
-__device__ __forceinline__ float2 mx_mul2(float2 a, float2 b) {
-    float2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;"
-        : "=l"(reinterpret_cast<unsigned long long&>(d))
-        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
-    return d;
-}
 // two f32 -> packed f16x2 with `a` in the low half, saturating to the finite range
 __device__ __forceinline__ uint32_t mx_pack(float a, float b) {
     uint32_t r;
@@ -174,12 +167,16 @@ __device__ __forceinline__ int mx_col_exp(unsigned bits) {
 
 // ------------------------------------------------------------ kernel --
 // One round: 8 recurrence steps of the lane's 4 points (two f32x2 pairs; point
-// k = 2 kp + {0: .x, 1: .y}); with SPLIT each value v is also split into
+// k = 2 kp + {0: .x, 1: .y}).  A point is carried as u = x - 1 and the
+// product x sigma as fma(u, sigma, sigma): u keeps full relative precision
+// next to the north pole, where x itself is within an FP32 spacing of 1 (the
+// interpolated route's samples need it; for catalog points, whose x is an
+// FP32 input, u = x - 1 is exact for x >= 1/2).  With SPLIT each value v is also split into
 //   hi  = v with its low 13 mantissa bits cleared (exact in fp16), 0 below range
 //   lo' = hi - v (the negated low part, exact in FP32, rounded to fp16), 0 below range
 // packed as fp16 pairs of consecutive steps.
 template <bool SPLIT>
-__device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&x2)[2], float2 (&p1)[2],
+__device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&u2)[2], float2 (&p1)[2],
                                          float2 (&p2)[2], const float2 (&nal)[2], const uint32_t (&mask)[4],
                                          uint32_t (&hi)[4][4], uint32_t (&lo)[4][4]) {
 #pragma unroll
@@ -189,14 +186,14 @@ __device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&
         float2 s0[2];
 #pragma unroll
         for (int kp = 0; kp < 2; ++kp) {
-            const float2 sg = mx_fma2(av0, mx_mul2(x2[kp], p1[kp]), p2[kp]);
+            const float2 sg = mx_fma2(av0, mx_fma2(u2[kp], p1[kp], p1[kp]), p2[kp]);
             p2[kp] = p1[kp];
             p1[kp] = sg;
             s0[kp] = sg;
         }
 #pragma unroll
         for (int kp = 0; kp < 2; ++kp) {
-            const float2 sg = mx_fma2(av1, mx_mul2(x2[kp], p1[kp]), p2[kp]);
+            const float2 sg = mx_fma2(av1, mx_fma2(u2[kp], p1[kp], p1[kp]), p2[kp]);
             p2[kp] = p1[kp];
             p1[kp] = sg;
         }
@@ -316,7 +313,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                 const float2* alpha2 = p.alpha2 + p.colstart[m];
                 const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
                 // ---- per-point seed, phase and state (4 points per lane) ----
-                float2 x2[2], p1[2], p2[2], nal[2];
+                float2 u2[2], p1[2], p2[2], nal[2];
                 uint32_t mask[4];
                 int E[4];
 #pragma unroll
@@ -331,12 +328,12 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     const float xv = tf[i];
                     const float na = E[k] == 0 ? -1.f : 0.f;
                     if (k & 1) {
-                        x2[k >> 1].y = xv;
+                        u2[k >> 1].y = xv;
                         p2[k >> 1].y = mant;
                         p1[k >> 1].y = 0.f;
                         nal[k >> 1].y = na;
                     } else {
-                        x2[k >> 1].x = xv;
+                        u2[k >> 1].x = xv;
                         p2[k >> 1].x = mant;
                         p1[k >> 1].x = 0.f;
                         nal[k >> 1].x = na;
@@ -354,20 +351,26 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                         const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
                         float wa, wb = 0.f;
                         if (p.vtab) {
-                            // table mode: column 0 = Vy^(m), 1 = h Vd^(m-1), 2 = h Vd^(m+1) of this sample
+                            // table mode: columns 3 half + {0: Vy^(m), 1: h Vd^(m-1), 2: h Vd^(m+1)}
+                            // of the sample pair at this position (half 0 north, 1 south)
                             const int64_t node = pt0 + (int64_t)t * MX_P + qbase + q;
-                            float2 wt = make_float2(0.f, 0.f);
-                            float f = 1.f;
-                            if (fa == 0) {
-                                wt = p.vtab[((int64_t)m * p.ntot + node) * 2];
-                            } else if (fa == 1 && m >= 1) {
-                                wt = p.vtab[((int64_t)(m - 1) * p.ntot + node) * 2 + 1];
-                                f = p.vtab_h;
-                            } else if (fa == 2 && m < L) {
-                                wt = p.vtab[((int64_t)(m + 1) * p.ntot + node) * 2 + 1];
-                                f = p.vtab_h;
-                            }
-                            wa = (comp ? wt.y : wt.x) * f * sca;
+                            auto tab = [&](int c) {
+                                const int half = c >= 3, ty = c - 3 * half;
+                                float2 wt = make_float2(0.f, 0.f);
+                                float f = 1.f;
+                                if (ty == 0) {
+                                    wt = p.vtab[((int64_t)m * p.ntot + node) * 4 + 2 * half];
+                                } else if (ty == 1 && m >= 1) {
+                                    wt = p.vtab[((int64_t)(m - 1) * p.ntot + node) * 4 + 2 * half + 1];
+                                    f = p.vtab_h;
+                                } else if (ty == 2 && m < L) {
+                                    wt = p.vtab[((int64_t)(m + 1) * p.ntot + node) * 4 + 2 * half + 1];
+                                    f = p.vtab_h;
+                                }
+                                return (comp ? wt.y : wt.x) * f;
+                            };
+                            wa = fa < p.ncol ? tab(fa) * sca : 0.f;
+                            if (NF == 8) wb = fb < p.ncol ? tab(fb) * scb : 0.f;
                         } else {
                             const float2 ph = my_ph[q];
                             const float trig = comp ? -ph.y : ph.x;
@@ -506,12 +509,12 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     };
                     if (mm && act) {
                         mmas();
-                        mx_round<true>(alr, x2, p1, p2, nal, mask, hi, lo);
+                        mx_round<true>(alr, u2, p1, p2, nal, mask, hi, lo);
                     } else if (act) {
-                        mx_round<true>(alr, x2, p1, p2, nal, mask, hi, lo);
+                        mx_round<true>(alr, u2, p1, p2, nal, mask, hi, lo);
                     } else {
                         if (mm) mmas();
-                        if (have) mx_round<false>(alr, x2, p1, p2, nal, mask, hi, lo);
+                        if (have) mx_round<false>(alr, u2, p1, p2, nal, mask, hi, lo);
                     }
                     if (act) {
 #pragma unroll
@@ -591,7 +594,7 @@ cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStr
 cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
     // exactly one weight source: prepared weight arrays or a table
     if ((mp.wcols == nullptr) == (mp.vtab == nullptr) || mp.ncol < 1 || mp.ncol > MX_MAXCOL ||
-        (mp.vtab && mp.ncol != 3))
+        (mp.vtab && mp.ncol != 6))
         return cudaErrorInvalidValue;
     const int nf = mp.ncol <= 4 ? 4 : 8;
     const size_t smem = mixed_smem_bytes(nf);
