@@ -44,6 +44,7 @@ int64_t mixed_acc_stride(int);
 cudaError_t launch_mixed_prep(const PrepColsParams&, int64_t, cudaStream_t);
 cudaError_t launch_mixed(const MixedParams&, int, cudaStream_t);
 int64_t interp_nranges(int64_t);
+int64_t interp_range();
 cudaError_t launch_interp_sort(const InterpParams&, cudaStream_t);
 cudaError_t launch_interp_tables(const InterpParams&, int, cudaStream_t);
 cudaError_t launch_interp_combine(int, int64_t, const double*, double*, cudaStream_t);
@@ -744,7 +745,8 @@ struct InterpLayout {
     int64_t npts_max = 0, nranges_max = 0, ntot = 0, chunk = 0, nunits = 0;
     int32_t nb = 0, nchunk = 0, npairs = 0, maxctas = 0;
     int64_t accstride = 0;
-    size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, v_off = 0, vtab_off = 0,
+    size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, stage_off = 0, v_off = 0,
+           vtab_off = 0,
            nodes_off = 0, colmax_off = 0, slots_off = 0, acc_off = 0, counter_off = 0, T_off = 0, total = 0;
 };
 
@@ -781,6 +783,7 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
     c.total_off = b;  b += up256((size_t)c.nb * 8);
     c.wc_off = b;     b += up256((size_t)np * 4 * 4);
     c.turn_off = b;   b += up256((size_t)np * 2 * 4);
+    c.stage_off = b;  b += up256((size_t)std::max<int64_t>(c.nranges_max, 1) * interp_range() * 7 * 4);
     c.v_off = b;      b += up256((size_t)(L + 1) * c.nb * 4 * 8);
     c.vtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 4 * 8);
     c.nodes_off = b;  b += up256((size_t)c.ntot * mixed_geometry_arrays() * 4);
@@ -863,6 +866,7 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
         ip.total = reinterpret_cast<int64_t*>(ws + c.total_off);
         ip.wc = reinterpret_cast<float*>(ws + c.wc_off);
         ip.turn = reinterpret_cast<uint32_t*>(ws + c.turn_off);
+        ip.stage = reinterpret_cast<uint32_t*>(ws + c.stage_off);
         ip.v = reinterpret_cast<float2*>(ws + c.v_off);
         ip.vtab = reinterpret_cast<float2*>(ws + c.vtab_off);
         ip.nodes = reinterpret_cast<uint32_t*>(ws + c.nodes_off);

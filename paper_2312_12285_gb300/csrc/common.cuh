@@ -232,6 +232,7 @@ struct InterpParams {
     int64_t* total;                     // [nb]
     float* wc;                          // [4][npts] w coeff c_alpha, interval order
     uint32_t* turn;                     // [2][npts]
+    uint32_t* stage;                    // [7][npts] bucket, w coeff c_alpha, turn; catalog order
     float2* v;                          // [(lmax+1)][nb][4]
     float2* vtab;                       // [(lmax+1)][ntot][4]: (Vy, Vd) north, (Vy, Vd) south per position
     uint32_t* nodes;                    // [5][ntot] sample geometry (x, lsh, lsl, turn hi, lo)

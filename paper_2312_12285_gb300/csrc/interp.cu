@@ -32,8 +32,9 @@
 // is applied in the combination.  Positions carry u = x - 1 = -2 sin^2(s/2),
 // exact to FP32 relative precision next to the pole.
 //
-// Kernels: ip_hist / ip_scan_* / ip_scatter (stable counting sort of the
-// points by interval, deterministic), ip_bin (binning, one warp per
+// Kernels: ip_prep (per-point interval, spline weights, turn), ip_hist /
+// ip_scan_* / ip_scatter (stable counting sort of the points by interval,
+// deterministic), ip_bin (binning, one warp per
 // (interval, block of 256 orders), lanes over m, phases by exact fixed-point
 // turns and a 32-step rotation), ip_fold (sample weights Vy, Vd in |x|
 // order, column maxima), ip_nodes (sample geometry) and ip_combine.
@@ -66,6 +67,39 @@ __device__ __forceinline__ bool ip_range_of(const InterpParams& p, int64_t r, in
 }
 
 // ------------------------------------------------------ counting sort --
+// Per point, in the field's catalog order (index = range * IP_RANGE + offset,
+// ranges numbered across catalogs): bucket (interval + 1), w coeff c_alpha(t)
+// and the phi turn.  All FP64 arithmetic of the preparation happens here, in
+// a fully parallel grid; the sort kernels below only count and move words.
+__global__ void __launch_bounds__(256) ip_prep_kernel(const __grid_constant__ InterpParams p) {
+    const int64_t nslot = p.nranges * IP_RANGE;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nslot; e += (int64_t)gridDim.x * blockDim.x) {
+        int c;
+        int64_t i0, i1;
+        const int64_t r = e / IP_RANGE;
+        if (!ip_range_of(p, r, c, i0, i1)) continue;
+        const int64_t i = i0 + (e - r * IP_RANGE);
+        if (i >= i1) continue;
+        const InterpCat& cd = p.cat[c];
+        const float x = cd.x[i], ph = cd.phi[i], w = cd.w[i];
+        const bool ok = isfinite(x) && isfinite(ph) && isfinite(w) && fabsf(x) <= 1.f;
+        if (!ok) atomicOr(p.err, ERR_RANGE);
+        double t;
+        const int b = ip_interval(ok ? x : 0.f, p.ntheta, t) + 1;
+        const double wv = ok ? cd.coeff * (double)w : 0.0;
+        const double v = 1.0 - t;
+        const uint64_t turn = phi_to_turn(ok ? (double)ph : 0.0);
+        const int64_t S = p.nranges * IP_RANGE;
+        p.stage[e] = (uint32_t)b;
+        p.stage[S + e] = __float_as_uint((float)(wv * (2.0 * t + 1.0) * v * v));
+        p.stage[2 * S + e] = __float_as_uint((float)(wv * t * v * v));
+        p.stage[3 * S + e] = __float_as_uint((float)(wv * t * t * (3.0 - 2.0 * t)));
+        p.stage[4 * S + e] = __float_as_uint((float)(wv * t * t * (t - 1.0)));
+        p.stage[5 * S + e] = (uint32_t)(turn >> 32);
+        p.stage[6 * S + e] = (uint32_t)(turn & 0xffffffffu);
+    }
+}
+
 __global__ void __launch_bounds__(256) ip_hist_kernel(const __grid_constant__ InterpParams p) {
     extern __shared__ int cnt[];
     const int64_t r = blockIdx.x;
@@ -74,10 +108,8 @@ __global__ void __launch_bounds__(256) ip_hist_kernel(const __grid_constant__ In
     int c;
     int64_t i0, i1;
     if (ip_range_of(p, r, c, i0, i1)) {
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            double t;
-            atomicAdd(&cnt[ip_interval(p.cat[c].x[i], p.ntheta, t) + 1], 1);
-        }
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+            atomicAdd(&cnt[p.stage[r * IP_RANGE + (i - i0)]], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < p.nb; b += blockDim.x) p.hist[r * p.nb + b] = cnt[b];
@@ -133,24 +165,22 @@ __global__ void __launch_bounds__(32) ip_scatter_kernel(const __grid_constant__ 
     int c;
     int64_t i0, i1;
     if (!ip_range_of(p, r, c, i0, i1)) return;
-    const InterpCat& cd = p.cat[c];
+    const int64_t S = p.nranges * IP_RANGE;
+    const int64_t e0 = r * IP_RANGE - i0;  // stage slot of point i is e0 + i
     constexpr int U = 4;
     for (int64_t base = i0; base < i1; base += 32 * U) {
-        float xs[U], ps[U], ws[U];
+        uint32_t v[U][7];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = base + 32 * u + lane;
-            const bool valid = i < i1;
-            xs[u] = valid ? cd.x[i] : 0.f;
-            ps[u] = valid ? cd.phi[i] : 0.f;
-            ws[u] = valid ? cd.w[i] : 0.f;
+#pragma unroll
+            for (int a = 0; a < 7; ++a) v[u][a] = i < i1 ? p.stage[a * S + e0 + i] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = base + 32 * u + lane;
             const bool valid = i < i1;
-            double t = 0.0;
-            const int b = valid ? ip_interval(xs[u], p.ntheta, t) + 1 : -1;
+            const int b = valid ? (int)v[u][0] : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, b);
             const int rank = __popc(peers & ((1u << lane) - 1u));
             int64_t dst = 0;
@@ -159,23 +189,27 @@ __global__ void __launch_bounds__(32) ip_scatter_kernel(const __grid_constant__ 
             if (valid && rank == 0) next[b] += __popc(peers);
             __syncwarp();
             if (valid) {
-                const bool ok = isfinite(xs[u]) && isfinite(ps[u]) && isfinite(ws[u]) && fabsf(xs[u]) <= 1.f;
-                if (!ok) atomicOr(p.err, ERR_RANGE);
-                const double wv = ok ? cd.coeff * (double)ws[u] : 0.0;
-                const double v = 1.0 - t;
-                p.wc[dst] = (float)(wv * (2.0 * t + 1.0) * v * v);
-                p.wc[p.npts + dst] = (float)(wv * t * v * v);
-                p.wc[2 * p.npts + dst] = (float)(wv * t * t * (3.0 - 2.0 * t));
-                p.wc[3 * p.npts + dst] = (float)(wv * t * t * (t - 1.0));
-                const uint64_t turn = phi_to_turn(ok ? (double)ps[u] : 0.0);
-                p.turn[dst] = (uint32_t)(turn >> 32);
-                p.turn[p.npts + dst] = (uint32_t)(turn & 0xffffffffu);
+                reinterpret_cast<uint32_t*>(p.wc)[dst] = v[u][1];
+                reinterpret_cast<uint32_t*>(p.wc)[p.npts + dst] = v[u][2];
+                reinterpret_cast<uint32_t*>(p.wc)[2 * p.npts + dst] = v[u][3];
+                reinterpret_cast<uint32_t*>(p.wc)[3 * p.npts + dst] = v[u][4];
+                p.turn[dst] = v[u][5];
+                p.turn[p.npts + dst] = v[u][6];
             }
         }
     }
 }
 
 // -------------------------------------------------------------- binning --
+__device__ __forceinline__ float2 mx_fma2_ip(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)),
+          "l"(reinterpret_cast<unsigned long long&>(c)));
+    return d;
+}
+
 // v^(m)_{j alpha} for one interval and 256 orders per warp: lane l holds
 // m = 256 c + l + 32 k, k = 0..7, as (re, im) of the 4 alpha.
 __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ InterpParams p) {
@@ -186,29 +220,29 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
     for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < ntask; task += nwarp) {
         const int b = (int)(task / nch), c = (int)(task - (int64_t)(task / nch) * nch);
         const int m0 = IP_MCHUNK * c + lane;
-        float vr[8][4], vi[8][4];
+        // per m: (re, im) of the alpha pairs {0, 1} and {2, 3} as f32x2 lanes
+        float2 vr01[8], vi01[8], vr23[8], vi23[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) vr[k][a] = vi[k][a] = 0.f;
+        for (int k = 0; k < 8; ++k) vr01[k] = vi01[k] = vr23[k] = vi23[k] = make_float2(0.f, 0.f);
         const int64_t r0 = p.binoff[b], r1 = p.binoff[b + 1];
         for (int64_t r = r0; r < r1; ++r) {
-            const float w0 = p.wc[r], w1 = p.wc[p.npts + r], w2 = p.wc[2 * p.npts + r], w3 = p.wc[3 * p.npts + r];
+            const float2 w01 = make_float2(p.wc[r], p.wc[p.npts + r]);
+            const float2 w23 = make_float2(p.wc[2 * p.npts + r], p.wc[3 * p.npts + r]);
+            const float2 nw01 = make_float2(-w01.x, -w01.y), nw23 = make_float2(-w23.x, -w23.y);
             const uint32_t th = p.turn[r], tl = p.turn[p.npts + r];
-            float cs, sn, c32, s32;
+            float cs, sn, c32 = 0.f, s32 = 0.f;
             phase_f32(m0, th, tl, cs, sn);
-            phase_f32(32, th, tl, c32, s32);
+            if (lane == 0) phase_f32(32, th, tl, c32, s32);  // the 32-order step, shared by all lanes
+            c32 = __shfl_sync(0xffffffffu, c32, 0);
+            s32 = __shfl_sync(0xffffffffu, s32, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 // w c_alpha e^{-i m phi} = w c_alpha (cos - i sin)
-                vr[k][0] = fmaf(w0, cs, vr[k][0]);
-                vi[k][0] = fmaf(-w0, sn, vi[k][0]);
-                vr[k][1] = fmaf(w1, cs, vr[k][1]);
-                vi[k][1] = fmaf(-w1, sn, vi[k][1]);
-                vr[k][2] = fmaf(w2, cs, vr[k][2]);
-                vi[k][2] = fmaf(-w2, sn, vi[k][2]);
-                vr[k][3] = fmaf(w3, cs, vr[k][3]);
-                vi[k][3] = fmaf(-w3, sn, vi[k][3]);
+                const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn);
+                vr01[k] = mx_fma2_ip(w01, c2, vr01[k]);
+                vi01[k] = mx_fma2_ip(nw01, s2, vi01[k]);
+                vr23[k] = mx_fma2_ip(w23, c2, vr23[k]);
+                vi23[k] = mx_fma2_ip(nw23, s2, vi23[k]);
                 const float cn = fmaf(cs, c32, -sn * s32);
                 sn = fmaf(sn, c32, cs * s32);
                 cs = cn;
@@ -219,8 +253,8 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
             const int m = m0 + 32 * k;
             if (m <= p.lmax) {
                 float4* dst = reinterpret_cast<float4*>(p.v + ((int64_t)m * p.nb + b) * 4);
-                dst[0] = make_float4(vr[k][0], vi[k][0], vr[k][1], vi[k][1]);
-                dst[1] = make_float4(vr[k][2], vi[k][2], vr[k][3], vi[k][3]);
+                dst[0] = make_float4(vr01[k].x, vi01[k].x, vr01[k].y, vi01[k].y);
+                dst[1] = make_float4(vr23[k].x, vi23[k].x, vr23[k].y, vi23[k].y);
             }
         }
     }
@@ -356,15 +390,20 @@ __global__ void ip_combine_kernel(int lmax, int64_t nmodes, const double2* T, do
 
 // ------------------------------------------------------------ launchers --
 int64_t interp_nranges(int64_t n) { return (n + IP_RANGE - 1) / IP_RANGE; }
+int64_t interp_range() { return IP_RANGE; }
 
 cudaError_t launch_interp_sort(const InterpParams& p, cudaStream_t st) {
     if (p.nranges == 0) {
         // no points: empty intervals
         return cudaMemsetAsync(p.binoff, 0, (size_t)(p.nb + 1) * sizeof(int64_t), st);
     }
+    const int64_t pblocks = (p.nranges * IP_RANGE + 255) / 256;
+    ip_prep_kernel<<<(unsigned)(pblocks < 4096 ? pblocks : 4096), 256, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const size_t hs = (size_t)p.nb * sizeof(int);
     int occ = 0;
-    cudaError_t e = configure_kernel(reinterpret_cast<const void*>(ip_hist_kernel), 256, hs, &occ);
+    e = configure_kernel(reinterpret_cast<const void*>(ip_hist_kernel), 256, hs, &occ);
     if (e != cudaSuccess) return e;
     ip_hist_kernel<<<(unsigned)p.nranges, 256, hs, st>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
