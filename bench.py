@@ -280,10 +280,11 @@ def ours(args):
         return cl, cb
 
     # prep (pads, hist, scan, scatter), analysis, reduce, 2 x shot noise, [combine x2], C_l, bins
-    # interp: hist, 2 scans, scatter, bin, fold, [pad], samples, grid transform, reduce, combine; noise 2, C_l, bins
+    # interp: prep, hist, 2 scans, scatter, bin, fold, [pad], positions, transform, reduce, combine;
+    # then noise 2, C_l, bins
     launches_per_step = 10 + (2 if coef is not None else 0)
     if prec == "interp":
-        launches_per_step = nfield * (10 + (1 if nt % 1024 else 0)) + 4 + (2 if coef is not None else 0)
+        launches_per_step = nfield * (11 + (1 if (nt // 2) % 1024 else 0)) + 4 + (2 if coef is not None else 0)
 
     for _ in range(max(3, args.warmup)):
         step()
