@@ -242,11 +242,14 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
  * equispaced in theta, s_k = (k + 1/2) pi/ntheta, and each point takes the
  * cubic Hermite spline of its interval; the sum over points runs first, per
  * order m (binning of w e^{-i m phi} times the 4 spline weights into the
- * intervals), then a transform of the samples (the mixed tensor-core kernel
- * on three weight columns per sample) and an FP64 combination.  The samples
- * are in theta, not in x as in the paper: in theta y_lm stays smooth through
- * the poles when continued across them (y(-theta) = (-1)^m y(theta)), so the
- * two outer intervals use ghost samples and no point is treated apart.
+ * intervals), then a transform of the samples (the mixed tensor-core kernel;
+ * a sample and its mirror pi - theta share one position, six weight columns)
+ * and an FP64 combination.  The theta-derivative is taken in its
+ * order-coupled form (lambda at m +- 1), free of the 1/sin(theta)
+ * cancellation near the poles.  The samples are in theta, not in x as in the
+ * paper: in theta y_lm stays smooth through the poles when continued across
+ * them (y(-theta) = (-1)^m y(theta)), so the two outer intervals use ghost
+ * samples and no point is treated apart.
  * Error: the spline's O(h^4) interpolation error, about 2e-5 relative per
  * value at ntheta = 8 lmax and 1.5e-6 at 16 lmax (h = pi/ntheta), plus the
  * mixed path's rounding; work O(N lmax + ntheta lmax^2) instead of
@@ -254,8 +257,9 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
  * cats as for pointsht_alm with float x, phi, w (POINTSHT_FP32 layout);
  * ntheta even, 2 <= ntheta <= 32768; fewer than 2^31 points per field;
  * alm_out: device, nfield*M complex128; workspace: device, >=
- * pointsht_workspace_size_interp() bytes (~(lmax+1)(ntheta+1) x 56 bytes:
- * 3.8 GB at lmax 2048, ntheta 32768), 256-byte aligned, clobbered.
+ * pointsht_workspace_size_interp() bytes (~(lmax+1)(ntheta+1) x 48 bytes plus
+ * 36 bytes per point: 3.6 GB at lmax 2048, ntheta 32768, 1e7 points),
+ * 256-byte aligned, clobbered.
  * Errors as for pointsht_alm. */
 size_t pointsht_workspace_size_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
                                       int32_t nfield, int32_t ntheta);
