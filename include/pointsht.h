@@ -258,7 +258,7 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
  * ntheta even, 2 <= ntheta <= 32768; fewer than 2^31 points per field;
  * alm_out: device, nfield*M complex128; workspace: device, >=
  * pointsht_workspace_size_interp() bytes (~(lmax+1)(ntheta+1) x 48 bytes plus
- * 36 bytes per point: 3.6 GB at lmax 2048, ntheta 32768, 1e7 points),
+ * ~52 bytes per point: about 4.3 GB at lmax 2048, ntheta 32768, 1e7 points),
  * 256-byte aligned, clobbered.
  * Errors as for pointsht_alm. */
 size_t pointsht_workspace_size_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
