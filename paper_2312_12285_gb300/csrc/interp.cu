@@ -225,11 +225,31 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
 #pragma unroll
         for (int k = 0; k < 8; ++k) vr01[k] = vi01[k] = vr23[k] = vi23[k] = make_float2(0.f, 0.f);
         const int64_t r0 = p.binoff[b], r1 = p.binoff[b + 1];
+        // orders of this block that exist (the last block of the range may be partial)
+        const int kmax = min(8, (p.lmax - IP_MCHUNK * c) / 32 + 1);
+        // the next point's data is loaded one iteration ahead
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
+        uint32_t nth = 0u, ntl = 0u;
+        if (r0 < r1) {
+            n0 = p.wc[r0];
+            n1 = p.wc[p.npts + r0];
+            n2 = p.wc[2 * p.npts + r0];
+            n3 = p.wc[3 * p.npts + r0];
+            nth = p.turn[r0];
+            ntl = p.turn[p.npts + r0];
+        }
         for (int64_t r = r0; r < r1; ++r) {
-            const float2 w01 = make_float2(p.wc[r], p.wc[p.npts + r]);
-            const float2 w23 = make_float2(p.wc[2 * p.npts + r], p.wc[3 * p.npts + r]);
+            const float2 w01 = make_float2(n0, n1), w23 = make_float2(n2, n3);
+            const uint32_t th = nth, tl = ntl;
+            if (r + 1 < r1) {
+                n0 = p.wc[r + 1];
+                n1 = p.wc[p.npts + r + 1];
+                n2 = p.wc[2 * p.npts + r + 1];
+                n3 = p.wc[3 * p.npts + r + 1];
+                nth = p.turn[r + 1];
+                ntl = p.turn[p.npts + r + 1];
+            }
             const float2 nw01 = make_float2(-w01.x, -w01.y), nw23 = make_float2(-w23.x, -w23.y);
-            const uint32_t th = p.turn[r], tl = p.turn[p.npts + r];
             float cs, sn, c32 = 0.f, s32 = 0.f;
             phase_f32(m0, th, tl, cs, sn);
             if (lane == 0) phase_f32(32, th, tl, c32, s32);  // the 32-order step, shared by all lanes
@@ -237,6 +257,7 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
             s32 = __shfl_sync(0xffffffffu, s32, 0);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
+                if (k >= kmax) break;
                 // w c_alpha e^{-i m phi} = w c_alpha (cos - i sin)
                 const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn);
                 vr01[k] = mx_fma2_ip(w01, c2, vr01[k]);

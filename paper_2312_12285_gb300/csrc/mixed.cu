@@ -62,7 +62,7 @@ __device__ __forceinline__ void mx_write(const PrepColsParams& p, int64_t j, flo
     const uint64_t turn = phi_to_turn((double)ph);
     float* b = reinterpret_cast<float*>(p.pts);
     const float lh = (float)ls;
-    b[j] = x - 1.f;  // u = x - 1 (exact for x >= 1/2)
+    b[j] = x;
     b[p.ntot + j] = lh;
     b[2 * p.ntot + j] = (float)(ls - (double)lh);
     p.pts[3 * p.ntot + j] = (uint32_t)(turn >> 32);
@@ -128,6 +128,13 @@ __device__ __forceinline__ float2 mx_fma2(float2 a, float2 b, float2 c) {
           "l"(reinterpret_cast<unsigned long long&>(c)));
     return d;
 }
+__device__ __forceinline__ float2 mx_mul2(float2 a, float2 b) {
+    float2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
 // two f32 -> packed f16x2 with `a` in the low half, saturating to the finite range
 __device__ __forceinline__ uint32_t mx_pack(float a, float b) {
     uint32_t r;
@@ -167,15 +174,16 @@ __device__ __forceinline__ int mx_col_exp(unsigned bits) {
 
 // ------------------------------------------------------------ kernel --
 // One round: 8 recurrence steps of the lane's 4 points (two f32x2 pairs; point
-// k = 2 kp + {0: .x, 1: .y}).  A point is carried as u = x - 1 and the
-// product x sigma as fma(u, sigma, sigma): u keeps full relative precision
-// next to the north pole, where x itself is within an FP32 spacing of 1 (the
-// interpolated route's samples need it; for catalog points, whose x is an
-// FP32 input, u = x - 1 is exact for x >= 1/2).  With SPLIT each value v is also split into
+// k = 2 kp + {0: .x, 1: .y}).  With UF the point is carried as u = x - 1 and
+// the product x sigma formed as fma(u, sigma, sigma): u keeps full relative
+// precision next to the north pole, where x itself is within an FP32 spacing
+// of 1 (the interpolated route's samples, whose u is computed in FP64);
+// without UF (catalog points, whose x is an FP32 input) as x * sigma.  With
+// SPLIT each value v is also split into
 //   hi  = v with its low 13 mantissa bits cleared (exact in fp16), 0 below range
 //   lo' = hi - v (the negated low part, exact in FP32, rounded to fp16), 0 below range
 // packed as fp16 pairs of consecutive steps.
-template <bool SPLIT>
+template <bool SPLIT, bool UF>
 __device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&u2)[2], float2 (&p1)[2],
                                          float2 (&p2)[2], const float2 (&nal)[2], const uint32_t (&mask)[4],
                                          uint32_t (&hi)[4][4], uint32_t (&lo)[4][4]) {
@@ -186,14 +194,14 @@ __device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&
         float2 s0[2];
 #pragma unroll
         for (int kp = 0; kp < 2; ++kp) {
-            const float2 sg = mx_fma2(av0, mx_fma2(u2[kp], p1[kp], p1[kp]), p2[kp]);
+            const float2 sg = mx_fma2(av0, UF ? mx_fma2(u2[kp], p1[kp], p1[kp]) : mx_mul2(u2[kp], p1[kp]), p2[kp]);
             p2[kp] = p1[kp];
             p1[kp] = sg;
             s0[kp] = sg;
         }
 #pragma unroll
         for (int kp = 0; kp < 2; ++kp) {
-            const float2 sg = mx_fma2(av1, mx_fma2(u2[kp], p1[kp], p1[kp]), p2[kp]);
+            const float2 sg = mx_fma2(av1, UF ? mx_fma2(u2[kp], p1[kp], p1[kp]) : mx_mul2(u2[kp], p1[kp]), p2[kp]);
             p2[kp] = p1[kp];
             p1[kp] = sg;
         }
@@ -227,7 +235,7 @@ __device__ __forceinline__ void mx_split_w(float v, float& h, float& l) {
 // and row g of the result is (D1 - D2)[g] + D1[g + 8].  NF = 8: rows 0..15 =
 // fields 0..7 (re, im); A_hi and A_lo are separate fragments and
 //   D1 += A_hi . B_hi + A_lo . B_hi,   D2 += A_hi . B_lo',   result D1 - D2.
-template <int NF>
+template <int NF, bool UF>
 __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const __grid_constant__ MixedParams p) {
     constexpr int NV = 2 * NF;                 // values per l: (field, re/im)
     constexpr int PS = NV + 4;                 // row stride of the partial sums (bank-conflict-free stores)
@@ -509,12 +517,12 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     };
                     if (mm && act) {
                         mmas();
-                        mx_round<true>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
                     } else if (act) {
-                        mx_round<true>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
                     } else {
                         if (mm) mmas();
-                        if (have) mx_round<false>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        if (have) mx_round<false, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
                     }
                     if (act) {
 #pragma unroll
@@ -598,8 +606,10 @@ cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
         return cudaErrorInvalidValue;
     const int nf = mp.ncol <= 4 ? 4 : 8;
     const size_t smem = mixed_smem_bytes(nf);
-    const void* kern = nf == 4 ? reinterpret_cast<const void*>(analysis_mixed_kernel<4>)
-                               : reinterpret_cast<const void*>(analysis_mixed_kernel<8>);
+    // column mode: x from the catalogs; table mode: u = x - 1 of the interpolation samples
+    const void* kern = mp.vtab ? reinterpret_cast<const void*>(analysis_mixed_kernel<8, true>)
+                       : nf == 4 ? reinterpret_cast<const void*>(analysis_mixed_kernel<4, false>)
+                                 : reinterpret_cast<const void*>(analysis_mixed_kernel<8, false>);
     int occ = 0;
     cudaError_t e = configure_kernel(kern, MX_WARPS * 32, smem, &occ);
     if (e != cudaSuccess) return e;
@@ -608,8 +618,9 @@ cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
     if (grid > mp.nunits) grid = mp.nunits;
     if (grid > mp.maxctas) grid = mp.maxctas;
     if (grid < 1) grid = 1;
-    if (nf == 4) analysis_mixed_kernel<4><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
-    else analysis_mixed_kernel<8><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    if (mp.vtab) analysis_mixed_kernel<8, true><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    else if (nf == 4) analysis_mixed_kernel<4, false><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
+    else analysis_mixed_kernel<8, false><<<(int)grid, MX_WARPS * 32, smem, st>>>(mp);
     return cudaGetLastError();
 }
 
