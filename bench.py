@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--columns", type=int, default=0,
                     help="weight columns on the workload's point set (pointsht_alm_columns); 0 = catalog form")
     ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
@@ -414,6 +415,9 @@ def ours(args):
             oracle.rel_err_per_l(a[f], ref[f], L) for f in range(nfield)),
             "sample_points": npts, "definition": "max over 1<=l<=lmax of |C_l - C_l^ref| / C_l^ref"}
         ladder_sample = (sample, ref[0]) if nfield == 1 else None
+    adjoint = None
+    if rank == 0 and world == 1 and not args.no_adjoint and prec in ("fp32", "fp64") and coef is None:
+        adjoint = adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src)
     ladder = None
     if rank == 0 and world == 1 and not args.no_ladder and prec == "fp32" and wl.nfield == 1:
         ladder = precision_ladder(wl, plan, dev, value, accuracy["cl_err_vs_fp64_oracle"] if accuracy else None,
@@ -450,11 +454,52 @@ def ours(args):
             "clocks": clocks,
             "accuracy": accuracy,
             "precision_ladder": ladder,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src):
+    """The adjoint row: gradient of L = sum_b g_b C_b (32 log-spaced bandpowers,
+    shot noise removed) with respect to every weight, i.e. bin_backward ->
+    cl_backward -> alm_backward (the point-evaluation synthesis kernel), timed
+    with CUDA events after one warm-up."""
+    import numpy as np
+    import torch
+
+    from paper_2312_12285_gb300 import catalogs, ops
+    a = ops.alm_raw(plan, cats, nfield, prec, out=out, workspace=ws)
+    noise = ops.shot_noise_raw(cats, nfield, prec, a.device, workspace=ws)
+    a = a.clone()
+    gb = torch.from_numpy(catalogs.rng_for(5, 7).standard_normal((nfield * (nfield + 1) // 2, edges.shape[0] - 1))
+                          ).to(a.device)
+
+    def backward():
+        gcl = ops.bin_backward_raw(gb, edges, L)
+        galm, gnoise = ops.cl_backward_raw(a, gcl, want_noise=True)
+        return ops.alm_backward_raw(plan, cats, nfield, prec, galm, gnoise, workspace=ws)
+
+    backward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    grads = backward()
+    e1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1)
+    npts = sum(int(c.x.shape[0]) for c in cats)
+    nm = (L + 1) * (L + 2) // 2
+    ach = FLOPS_PER_POINT_MODE * npts * nm / (ms / 1e3) / 1e12
+    finite = bool(all(torch.isfinite(g).all() for g in grads))
+    return {"value": npts * nm / (ms / 1e3), "unit": UNIT, "ms": ms, "grad_finite": finite,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "kernel": "adjoint_kernel (point-evaluation synthesis, 7 flops per point x mode: "
+                                   "recurrence 3, accumulation 4)", "peak_source": peak_src},
+            "what": "d(sum_b g_b C_b)/dw_i for every object: bin_backward, cl_backward, alm_backward"}
 
 
 # ------------------------------------------------------- weight columns --
