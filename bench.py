@@ -497,7 +497,9 @@ def adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src)
     finite = bool(all(torch.isfinite(g).all() for g in grads))
     return {"value": npts * nm / (ms / 1e3), "unit": UNIT, "ms": ms, "grad_finite": finite,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "kernel": "adjoint_kernel (point-evaluation synthesis, 7 flops per point x mode: "
+                         "kernel": ("adjoint_sorted_kernel (|x|-sorted, packed f32x2" if prec == "fp32" else
+                                    "adjoint_kernel (catalog order") +
+                                   "; point-evaluation synthesis, 7 flops per point x mode: "
                                    "recurrence 3, accumulation 4)", "peak_source": peak_src},
             "what": "d(sum_b g_b C_b)/dw_i for every object: bin_backward, cl_backward, alm_backward"}
 

@@ -242,6 +242,207 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const __grid_constant__ Ad
     }
 }
 
+__device__ __forceinline__ float2 adj_fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)),
+          "l"(reinterpret_cast<unsigned long long&>(c)));
+    return d;
+}
+__device__ __forceinline__ float2 adj_mul2(float2 a, float2 b) {
+    float2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
+
+// FP32 adjoint over the points as prepared (and |x|-sorted) for the analysis:
+// a warp takes 32 K consecutive prepared points of one field, K = 8 per lane
+// as four f32x2 pairs, so that the points of a warp cross into the FP32
+// range together and a warp all of whose points are below it runs the
+// recurrence only.  Per step and pair: x sigma (mul2), the recurrence (fma2)
+// and the two accumulations (fma2 with (gamma g re, same) and (im, im)).
+// The gradient goes back to each point's catalog and index through the
+// prepared point id.
+constexpr int ADJ_KP = 4;                 // f32x2 pairs per lane
+constexpr int ADJ_PW = 32 * 2 * ADJ_KP;   // points per warp (256)
+
+__global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_constant__ AdjointParams p) {
+    constexpr int KP = ADJ_KP, K = 2 * ADJ_KP;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t start = gw * ADJ_PW;
+    if (start >= p.ntot) return;
+    int f = 0;
+    while (f + 1 < p.nfield && p.fld[f + 1].off <= start) ++f;
+    const float* tf = reinterpret_cast<const float*>(p.pts);
+    const uint32_t* tu = p.pts;
+    const int64_t N = p.ntot;
+    const int L = p.lmax;
+
+    float2 x2[KP];
+    float lh[K], ll[K];
+    uint32_t thi[K], tlo[K];
+    double tot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t i = start + 32 * k + lane;
+        const float xv = tf[i];
+        if (k & 1) x2[k >> 1].y = xv;
+        else x2[k >> 1].x = xv;
+        lh[k] = tf[2 * N + i];
+        ll[k] = tf[3 * N + i];
+        thi[k] = tu[4 * N + i];
+        tlo[k] = tu[5 * N + i];
+        tot[k] = 0.0;
+    }
+    const float4* gtab = static_cast<const float4*>(p.gtab) + (int64_t)f * p.gstride;
+
+    for (int m = 0; m <= L; ++m) {
+        const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
+        float2 p1[KP], p2[KP], ar[KP], ai[KP];
+        float cs[K], sn[K];
+        int E[K];
+        bool lane_neg = false, lane_dead = true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float mant;
+            seed_f32(m, lh[k], ll[k], lch, lcl, mant, E[k]);
+            phase_f32(m, thi[k], tlo[k], cs[k], sn[k]);
+            if (k & 1) {
+                p2[k >> 1].y = mant;  // with alpha_m = 0 the first step gives sigma_m = mant
+                p1[k >> 1].y = 0.f;
+            } else {
+                p2[k >> 1].x = mant;
+                p1[k >> 1].x = 0.f;
+            }
+            lane_neg |= E[k] < 0;
+            lane_dead &= E[k] < 0;
+        }
+#pragma unroll
+        for (int kp = 0; kp < KP; ++kp) ar[kp] = ai[kp] = make_float2(0.f, 0.f);
+        bool any_neg = __any_sync(0xffffffffu, lane_neg);
+        bool all_dead = __all_sync(0xffffffffu, lane_dead);
+        const int64_t cs0 = p.colstart[m];
+        const float2* al = p.alpha2 + cs0;
+        const float4* gc = gtab + cs0;
+        const int nblk = (L - m + 1 + 7) >> 3;
+        for (int bk = 0; bk < nblk; ++bk) {
+            float2 av[8];
+            float4 gv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                av[j] = __ldg(al + 8 * bk + j);
+                gv[j] = __ldg(gc + 8 * bk + j);
+            }
+            if (all_dead) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int kp = 0; kp < KP; ++kp) {
+                        const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
+                        p2[kp] = p1[kp];
+                        p1[kp] = mu;
+                    }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int kp = 0; kp < KP; ++kp) {
+                        const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
+                        p2[kp] = p1[kp];
+                        p1[kp] = mu;
+                        ar[kp] = adj_fma2(mu, make_float2(gv[j].x, gv[j].y), ar[kp]);
+                        ai[kp] = adj_fma2(mu, make_float2(gv[j].z, gv[j].w), ai[kp]);
+                    }
+            }
+            if (any_neg) {
+                // rescale check every 8 steps (F32Scale; 8-step growth <= 2^42)
+                lane_neg = false;
+                lane_dead = true;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
+                    float& b = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
+                    if (E[k] < 0 && fmaxf(fabsf(a), fabsf(b)) > 0x1p-61f) {
+                        a *= 0x1p-64f;
+                        b *= 0x1p-64f;
+                        E[k] += 1;
+                        if (E[k] == 0) {  // drop what was summed below range
+                            if (k & 1) {
+                                ar[k >> 1].y = 0.f;
+                                ai[k >> 1].y = 0.f;
+                            } else {
+                                ar[k >> 1].x = 0.f;
+                                ai[k >> 1].x = 0.f;
+                            }
+                        }
+                    }
+                    lane_neg |= E[k] < 0;
+                    lane_dead &= E[k] < 0;
+                }
+                any_neg = __any_sync(0xffffffffu, lane_neg);
+                all_dead = __all_sync(0xffffffffu, lane_dead);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float r = (k & 1) ? ar[k >> 1].y : ar[k >> 1].x;
+            const float im = (k & 1) ? ai[k >> 1].y : ai[k >> 1].x;
+            if (E[k] == 0) tot[k] += (double)cs[k] * (double)r - (double)sn[k] * (double)im;
+        }
+    }
+    const double gn = p.gnoise ? p.gnoise[(int64_t)f * (p.nfield + 1)] : 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t i = start + 32 * k + lane;
+        const uint32_t id = tu[6 * N + i];
+        if (id == 0xffffffffu) continue;  // padding
+        int c = 0;
+        while (c + 1 < p.ncat && (uint64_t)p.cat[c + 1].id0 <= (uint64_t)id) ++c;
+        const int64_t idx = (int64_t)id - p.cat[c].id0;
+        const double cw = (double)tf[N + i];  // coeff * w (0 for a point flagged out of range)
+        const double coeff = p.cat[c].coeff;
+        const double g = coeff * tot[k] + 2.0 * coeff * cw * gn / (4.0 * CUDART_PI);
+        static_cast<float*>(p.gradw[c])[idx] = (float)g;
+    }
+}
+
+// gtab entries for the sorted FP32 adjoint: (gamma g re, same, gamma g im, same)
+__global__ void build_gtab4_kernel(int L, const double2* __restrict__ galm, const double* __restrict__ gamma,
+                                   const int64_t* __restrict__ colstart, int64_t gstride, float4* __restrict__ gtab) {
+    const int m = blockIdx.y, f = blockIdx.z;
+    const int64_t w = colstart[m + 1] - colstart[m];
+    const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < w; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m + q <= L) {
+            const int64_t idx = tri_base(m, L) + m + q;
+            const double2 g = galm[(int64_t)f * M + idx];
+            const double gm = gamma[idx];
+            v = make_float4((float)(g.x * gm), (float)(g.x * gm), (float)(g.y * gm), (float)(g.y * gm));
+        }
+        gtab[(int64_t)f * gstride + colstart[m] + q] = v;
+    }
+}
+
+int adjoint_sorted_points_per_warp() { return ADJ_PW; }
+
+cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, const double* gamma,
+                                  cudaStream_t st) {
+    dim3 grid(4, ap.lmax + 1, ap.nfield);
+    build_gtab4_kernel<<<grid, 256, 0, st>>>(ap.lmax, reinterpret_cast<const double2*>(galm), gamma, ap.colstart,
+                                             ap.gstride, (float4*)ap.gtab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nwarps = ap.ntot / ADJ_PW;
+    if (nwarps == 0) return cudaSuccess;
+    adjoint_sorted_kernel<<<(unsigned)((nwarps + 3) / 4), 128, 0, st>>>(ap);
+    return cudaGetLastError();
+}
+
 // gtab[f][colstart[m] + q] = gamma(l, m) * g^f(l, m), zero in the padding.
 template <typename R2>
 __global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const double* __restrict__ gamma,

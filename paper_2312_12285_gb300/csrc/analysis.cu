@@ -38,12 +38,14 @@ namespace psht {
 // ====================================================================
 //                           point preparation
 // ====================================================================
-// FP32 layout (6 arrays of 4 bytes, stride ntot):
-//   0 x, 1 coeff*w, 2 log2 sin(theta) hi, 3 lo, 4 turn[63:32], 5 turn[31:0]
+// FP32 layout (7 arrays of 4 bytes, stride ntot):
+//   0 x, 1 coeff*w, 2 log2 sin(theta) hi, 3 lo, 4 turn[63:32], 5 turn[31:0],
+//   6 point id (catalog id0 + index; 0xffffffff for padding; read by the adjoint)
 // FP64 layout (4 arrays of 8 bytes): 0 x, 1 coeff*w, 2 log2 sin(theta), 3 turn
 
 template <typename T>
-__device__ __forceinline__ void prep_one(const PrepParams& p, int64_t j, T x, T ph, T w, double coeff) {
+__device__ __forceinline__ void prep_one(const PrepParams& p, int64_t j, T x, T ph, T w, double coeff,
+                                         uint32_t id = 0xffffffffu) {
     bool ok = isfinite((double)x) && isfinite((double)ph) && isfinite((double)w) && fabs((double)x) <= 1.0;
     if (!ok) {
         atomicOr(p.err, ERR_RANGE);
@@ -66,6 +68,7 @@ __device__ __forceinline__ void prep_one(const PrepParams& p, int64_t j, T x, T 
         b[3 * p.ntot + j] = (float)(ls - (double)lh);
         bu[4 * p.ntot + j] = (uint32_t)(turn >> 32);
         bu[5 * p.ntot + j] = (uint32_t)(turn & 0xffffffffu);
+        bu[6 * p.ntot + j] = id;
     } else {
         double* b = static_cast<double*>(p.pts);
         uint64_t* bu = static_cast<uint64_t*>(p.pts);
@@ -86,7 +89,8 @@ __global__ void prep_kernel(const __grid_constant__ PrepParams p) {
         const T* xs = static_cast<const T*>(c.x);
         const T* ps = static_cast<const T*>(c.phi);
         const T* ws = static_cast<const T*>(c.w);
-        for (int64_t i = i0; i < c.n; i += stride) prep_one<T>(p, c.dst + i, xs[i], ps[i], ws[i], c.coeff);
+        for (int64_t i = i0; i < c.n; i += stride)
+            prep_one<T>(p, c.dst + i, xs[i], ps[i], ws[i], c.coeff, (uint32_t)(c.id0 + i));
     } else {
         const int f = seg - p.ncat;
         for (int64_t i = i0; i < p.pad_n[f]; i += stride) prep_one<T>(p, p.pad_off[f] + i, T(0), T(0), T(0), 0.0);
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(256) sort_scatter_kernel(const __grid_constant
         if (valid) {
             int64_t dst = next[bk] + rank;
             for (int w = 0; w < warp; ++w) dst += wcnt[w][bk];
-            prep_one<T>(sp.prep, dst, x, ps[i], ws[i], cd.coeff);
+            prep_one<T>(sp.prep, dst, x, ps[i], ws[i], cd.coeff, (uint32_t)(cd.id0 + i));
         }
         __syncthreads();
         for (int b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) {

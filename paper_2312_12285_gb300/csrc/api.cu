@@ -35,6 +35,8 @@ cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const
                               cudaStream_t);
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
+int adjoint_sorted_points_per_warp();
+cudaError_t launch_adjoint_sorted(const AdjointParams&, const double*, const double*, cudaStream_t);
 cudaError_t launch_sort_offsets_f32(const SortParams&, cudaStream_t);
 size_t mixed_smem_bytes(int);
 int mixed_tile_points();
@@ -344,7 +346,11 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     }
     if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
-    lo.narr = is_f64 ? 4 : 6;
+    if (!is_f64) {  // fields padded to whole warps of the FP32 adjoint as well
+        const int64_t q = adjoint_sorted_points_per_warp();
+        while (lo.P % q) lo.P += analysis_tile_points(is_f64, lo.k32);
+    }
+    lo.narr = is_f64 ? 4 : 7;
     lo.abytes = is_f64 ? 8 : 4;
     const int L = plan->lmax;
     lo.ngroups = (L / 2 + 1 + WARPS - 1) / WARPS;
@@ -393,8 +399,13 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     lo.hist_off = b;
     b += up256((size_t)std::max<int64_t>(lo.nranges, 1) * SORT_BUCKETS * 8);
     lo.fwd_end = b;
-    lo.gtab_off = 0;
-    lo.bwd_end = up256((size_t)nfield * plan->acol * 2 * lo.abytes);
+    if (is_f64) {  // catalog-order adjoint: the table alone
+        lo.gtab_off = 0;
+        lo.bwd_end = up256((size_t)nfield * plan->acol * 2 * lo.abytes);
+    } else {  // sorted adjoint: the prepared points, then float4 table entries
+        lo.gtab_off = lo.fwd_end;
+        lo.bwd_end = lo.gtab_off + up256((size_t)nfield * plan->acol * 16);
+    }
     lo.shot_off = 0;
     const size_t shot_end = up256((size_t)std::max(ncat, 1) * SHOT_NBLK * 8);
     lo.total = std::max(std::max(lo.fwd_end, lo.bwd_end), shot_end);
@@ -435,8 +446,11 @@ static void fill_prep(const pointsht_catalog* cats, int32_t ncat, int32_t nfield
     pp.pts = pts;
     pp.err = err;
     int64_t run[PSHT_MAX_FIELDS] = {};
+    int64_t id = 0;
     for (int c = 0; c < ncat; ++c) {
         const int f = cats[c].field;
+        pp.cat[c].id0 = id;
+        id += cats[c].n;
         pp.cat[c].x = cats[c].x;
         pp.cat[c].phi = cats[c].phi;
         pp.cat[c].w = cats[c].w;
@@ -1034,14 +1048,59 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
     void* gtab = ws + lo.gtab_off;
-    cudaError_t e = launch_build_gtab(lo.is_f64, plan->lmax, nfield, grad_alm, plan->gamma, plan->colstart,
-                                      plan->acol, gtab, st);
-    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: table: %s", cudaGetErrorString(e));
+    cudaError_t e;
     AdjointParams ap;
     memset(&ap, 0, sizeof(ap));
     ap.lmax = plan->lmax;
     ap.ncat = ncat;
     ap.nfield = nfield;
+    ap.gstride = plan->acol;
+    ap.colstart = plan->colstart;
+    ap.log2c_hi = plan->log2c_hi;
+    ap.log2c_lo = plan->log2c_lo;
+    ap.log2c = plan->log2c;
+    ap.gnoise = grad_noise;
+    ap.err = plan->err;
+    ap.gtab = gtab;
+    if (!lo.is_f64) {
+        // FP32: the points are prepared and |x|-sorted as for the analysis
+        // (point ids kept), then one warp runs 256 consecutive prepared points.
+        int64_t npts = 0;
+        for (int c = 0; c < ncat; ++c) npts += cats[c].n;
+        if (npts >= (int64_t)0xffffffffLL)
+            return fail(POINTSHT_EINVAL, "alm_backward: %lld points; the FP32 adjoint takes fewer than 2^32 - 1",
+                        (long long)npts);
+        PrepParams pp;
+        fill_prep(cats, ncat, nfield, lo, ws + lo.pts_off, plan->err, pp);
+        if (lo.ntot > 0) {
+            SortParams sp;
+            memset(&sp, 0, sizeof(sp));
+            sp.prep = pp;
+            int64_t r = 0;
+            for (int c = 0; c < ncat; ++c) {
+                sp.range0[c] = r;
+                r += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
+            }
+            sp.range0[ncat] = r;
+            for (int f = 0; f < nfield; ++f) sp.field_off[f] = lo.off[f];
+            sp.hist = reinterpret_cast<int64_t*>(ws + lo.hist_off);
+            e = launch_prep_sorted<float>(sp, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: prep launch: %s", cudaGetErrorString(e));
+        }
+        for (int c = 0; c < ncat; ++c) {
+            ap.cat[c] = pp.cat[c];
+            ap.gradw[c] = grad_w[c];
+        }
+        ap.pts = reinterpret_cast<const uint32_t*>(ws + lo.pts_off);
+        ap.ntot = lo.ntot;
+        for (int f = 0; f < nfield; ++f) ap.fld[f].off = lo.off[f];
+        ap.alpha2 = plan->alpha_f2;
+        e = launch_adjoint_sorted(ap, grad_alm, plan->gamma, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
+        return POINTSHT_OK;
+    }
+    e = launch_build_gtab(lo.is_f64, plan->lmax, nfield, grad_alm, plan->gamma, plan->colstart, plan->acol, gtab, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: table: %s", cudaGetErrorString(e));
     const int ppw = adjoint_points_per_warp(lo.is_f64);
     int64_t wsum = 0;
     for (int c = 0; c < ncat; ++c) {
@@ -1056,15 +1115,7 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
         wsum += (cats[c].n + ppw - 1) / ppw;
     }
     ap.warp0[ncat] = wsum;
-    ap.gtab = gtab;
-    ap.gstride = plan->acol;
-    ap.alpha = lo.is_f64 ? static_cast<const void*>(plan->alpha_d) : static_cast<const void*>(plan->alpha_f);
-    ap.colstart = plan->colstart;
-    ap.log2c_hi = plan->log2c_hi;
-    ap.log2c_lo = plan->log2c_lo;
-    ap.log2c = plan->log2c;
-    ap.gnoise = grad_noise;
-    ap.err = plan->err;
+    ap.alpha = plan->alpha_d;
     e = launch_adjoint(lo.is_f64, ap, st);
     if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
     return POINTSHT_OK;

@@ -125,6 +125,7 @@ struct CatDesc {
     double coeff;
     int32_t field;
     int32_t pad_;
+    int64_t id0;   // point id of this catalog's first point (catalogs numbered consecutively)
 };
 
 struct PrepParams {
@@ -254,6 +255,13 @@ struct AdjointParams {
     const double* gnoise;               // [nfield][nfield] dL/dN (diagonal used) or null
     void* gradw[PSHT_MAX_CATS];
     unsigned* err;
+    // FP32: the points as prepared for the analysis (|x| order, 7 arrays of
+    // ntot, array 6 = point id), fields at fld[].off; gtab entries float4
+    // (gamma g re, same, gamma g im, same)
+    const uint32_t* pts;
+    int64_t ntot;
+    FieldDesc fld[PSHT_MAX_FIELDS];
+    const float2* alpha2;
 };
 
 __host__ __device__ inline int64_t tri_base(int64_t m, int64_t lmax) {
