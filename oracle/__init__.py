@@ -57,6 +57,12 @@ def _load():
             lib.oracle_alm.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_threej000.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.oracle_threej000.restype = ctypes.c_double
+            lib.oracle_coupling.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
+            lib.oracle_coupling.restype = ctypes.c_int
+            lib.oracle_coupling_row.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp]
+            lib.oracle_coupling_row.restype = ctypes.c_int
             lib.oracle_hermite_basis.argtypes = [ctypes.c_double, dp]
             lib.oracle_hermite_basis.restype = None
             lib.oracle_alm_interp.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
@@ -275,3 +281,67 @@ def alm_interp(x, phi, w, lmax: int, ntheta: int, nthreads: int = 0):
     if rc != 0:
         raise RuntimeError(f"oracle_alm_interp failed ({rc})")
     return out[0::2] + 1j * out[1::2]
+
+
+# ------------------------------------- Eq. wldef, Eq. chat, mode decoupling --
+def window_cl(w_alm, lmax: int, noise: float = 0.0) -> np.ndarray:
+    """W_l = (1/(2l+1)) sum_m |w_lm|^2 (Eq. wldef) of the window's a_lm (the
+    scaled randoms), minus an optional shot-noise constant (the footnote to
+    Eq. wldef: subtract it when few randoms estimate the window)."""
+    return cl(w_alm, w_alm, lmax) - noise
+
+
+def threej000(l1: int, l2: int, l3: int) -> float:
+    """(l1 l2 l3; 0 0 0) from its closed form (App. "Wigner 3j symbols")."""
+    return float(_load().oracle_threej000(int(l1), int(l2), int(l3)))
+
+
+def coupling(W, lmax: int, nthreads: int = 0) -> np.ndarray:
+    """M_ll' of Eq. chat, [lmax+1, lmax+1] row-major, from W_0..W_{lmax_w}
+    (lmax_w = len(W) - 1; W beyond it is taken as zero)."""
+    W = _f64(W)
+    M = np.empty((lmax + 1, lmax + 1), np.float64)
+    rc = _load().oracle_coupling(int(lmax), W.shape[0] - 1, _dptr(W), _dptr(M), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_coupling failed ({rc})")
+    return M
+
+
+def coupling_row(W, lmax: int, l: int) -> np.ndarray:
+    W = _f64(W)
+    row = np.empty(lmax + 1, np.float64)
+    rc = _load().oracle_coupling_row(int(lmax), W.shape[0] - 1, _dptr(W), int(l), _dptr(row))
+    if rc != 0:
+        raise RuntimeError(f"oracle_coupling_row failed ({rc})")
+    return row
+
+
+def binned_coupling(M, edges):
+    """R[b, l'] = sum_l theta_b^l M_ll' (theta_b^l = 1/Delta l in bin b) and
+    the binned coupling M_bb' = sum_{l' in b'} R[b, l'] (Sec. 2.1: the true
+    C_l piecewise constant on the same bins)."""
+    edges = np.asarray(edges, np.int64)
+    lmax = M.shape[0] - 1
+    T = bin_matrix(edges, lmax)
+    R = T @ M
+    nb = edges.size - 1
+    Mbb = np.empty((nb, nb))
+    for b2 in range(nb):
+        Mbb[:, b2] = R[:, edges[b2]:edges[b2 + 1]].sum(axis=1)
+    return R, Mbb
+
+
+def decouple(Mbb, R, cl_binned):
+    """Mode-decoupled bandpowers C~_b = sum_b' (M^-1)_bb' C^_b' (Eq.
+    mode_coupling) and the window matrix cal M_bl' = sum_b' (M^-1)_bb' R[b', l']
+    (Eq. expectation_value)."""
+    Minv = np.linalg.inv(Mbb)
+    return Minv, Minv @ R, np.asarray(cl_binned) @ Minv.T
+
+
+def fkp_norm(W) -> float:
+    """cal N = 1 / [sum_l' (2l'+1) W_l' / 4pi]: the normalisation that leaves a
+    shot-noise spectrum unchanged (Sec. 2.1, the FKP-like alternative)."""
+    W = np.asarray(W, np.float64)
+    l = np.arange(W.size)
+    return 1.0 / (np.sum((2 * l + 1) * W) / FOUR_PI)

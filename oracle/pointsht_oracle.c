@@ -433,3 +433,90 @@ int oracle_alm_interp(int64_t n, const double* x, const double* phi, const doubl
     free(cr);
     return status;
 }
+
+/* ------------------------------------------------------------------------
+ * Mode coupling (Eq. chat) and the Wigner 3j symbol with zero orders
+ * (App. "Wigner 3j symbols").
+ *
+ * For l1 + l2 + l3 = 2g even and the triangle condition met,
+ *   (l1 l2 l3; 0 0 0) = (-1)^g sqrt[(2g-2l1)! (2g-2l2)! (2g-2l3)! / (2g+1)!]
+ *                       g! / [(g-l1)! (g-l2)! (g-l3)!],
+ * zero otherwise: the textbook closed form for zero orders (the paper's
+ * recurrence in App. "Wigner 3j symbols" steps along it).  Factorials enter
+ * through a long-double table of log n! (lgammal), so each value carries
+ * about 1e-14 relative error up to l ~ 1e4.
+ *
+ *   M_ll' = (2l'+1)/(4 pi) sum_lambda (2 lambda + 1) (l l' lambda; 0 0 0)^2 W_lambda
+ * (Eq. chat), lambda over |l - l'| .. min(l + l', lmax_w), summed in
+ * increasing lambda with a Neumaier accumulator.
+ * ---------------------------------------------------------------------- */
+static long double* logfact_table(int nmax) {
+    long double* t = (long double*)malloc(sizeof(long double) * (size_t)(nmax + 1));
+    if (!t) return NULL;
+    for (int n = 0; n <= nmax; ++n) t[n] = lgammal((long double)n + 1.0L);
+    return t;
+}
+
+static double threej000_lf(const long double* lf, int l1, int l2, int l3) {
+    const int L = l1 + l2 + l3;
+    if (L & 1) return 0.0;
+    if (l3 < abs(l1 - l2) || l3 > l1 + l2) return 0.0;
+    const int g = L / 2;
+    const long double lg = 0.5L * (lf[2 * g - 2 * l1] + lf[2 * g - 2 * l2] + lf[2 * g - 2 * l3] - lf[2 * g + 1]) +
+                           lf[g] - lf[g - l1] - lf[g - l2] - lf[g - l3];
+    const double v = (double)expl(lg);
+    return (g & 1) ? -v : v;
+}
+
+double oracle_threej000(int l1, int l2, int l3) {
+    if (l1 < 0 || l2 < 0 || l3 < 0) return 0.0;
+    long double* lf = logfact_table(l1 + l2 + l3 + 1);
+    if (!lf) return NAN;
+    const double v = threej000_lf(lf, l1, l2, l3);
+    free(lf);
+    return v;
+}
+
+/* M[l * (lmax + 1) + l'] for 0 <= l, l' <= lmax from W[0..lmax_w]. */
+int oracle_coupling(int lmax, int lmax_w, const double* W, double* M, int nthreads) {
+    if (lmax < 0 || lmax_w < 0) return 1;
+    long double* lf = logfact_table(2 * lmax + lmax_w + 2);
+    if (!lf) return 2;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int l = 0; l <= lmax; ++l) {
+        for (int lp = 0; lp <= lmax; ++lp) {
+            nsum acc = {0.0, 0.0};
+            const int lo = abs(l - lp), hi = (l + lp < lmax_w) ? l + lp : lmax_w;
+            for (int lam = lo; lam <= hi; ++lam) {
+                const double tj = threej000_lf(lf, l, lp, lam);
+                if (tj == 0.0) continue;
+                nsum_add(&acc, (2.0 * lam + 1.0) * tj * tj * W[lam]);
+            }
+            M[(int64_t)l * (lmax + 1) + lp] = (2.0 * lp + 1.0) / (4.0 * ORACLE_PI) * nsum_val(&acc);
+        }
+    }
+    free(lf);
+    return 0;
+}
+
+/* One row l of M (for sampled checks at large lmax). */
+int oracle_coupling_row(int lmax, int lmax_w, const double* W, int l, double* row) {
+    if (lmax < 0 || lmax_w < 0 || l < 0 || l > lmax) return 1;
+    long double* lf = logfact_table(2 * lmax + lmax_w + 2);
+    if (!lf) return 2;
+    for (int lp = 0; lp <= lmax; ++lp) {
+        nsum acc = {0.0, 0.0};
+        const int lo = abs(l - lp), hi = (l + lp < lmax_w) ? l + lp : lmax_w;
+        for (int lam = lo; lam <= hi; ++lam) {
+            const double tj = threej000_lf(lf, l, lp, lam);
+            if (tj == 0.0) continue;
+            nsum_add(&acc, (2.0 * lam + 1.0) * tj * tj * W[lam]);
+        }
+        row[lp] = (2.0 * lp + 1.0) / (4.0 * ORACLE_PI) * nsum_val(&acc);
+    }
+    free(lf);
+    return 0;
+}
