@@ -54,6 +54,7 @@ def parse():
                     help="weight columns on the workload's point set (pointsht_alm_columns); 0 = catalog form")
     ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-coupling", action="store_true", help="skip the mode-coupling matrix measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
@@ -418,6 +419,9 @@ def ours(args):
     adjoint = None
     if rank == 0 and world == 1 and not args.no_adjoint and prec in ("fp32", "fp64") and coef is None:
         adjoint = adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src)
+    coupling = None
+    if rank == 0 and world == 1 and not args.no_coupling and prec == "fp32" and coef is None:
+        coupling = coupling_measure(plan, wl, dev, L)
     ladder = None
     if rank == 0 and world == 1 and not args.no_ladder and prec == "fp32" and wl.nfield == 1:
         ladder = precision_ladder(wl, plan, dev, value, accuracy["cl_err_vs_fp64_oracle"] if accuracy else None,
@@ -455,11 +459,63 @@ def ours(args):
             "accuracy": accuracy,
             "precision_ladder": ladder,
             "adjoint": adjoint,
+            "coupling": coupling,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def coupling_terms(L: int, Lw: int) -> int:
+    """Terms of Eq. chat the coupling kernel sums: pairs l <= l' <= L, lambda
+    from l' - l to min(l + l', Lw) in steps of 2 (the parity of l + l')."""
+    import numpy as np
+    lp = np.arange(L + 1)
+    tot = 0
+    for l in range(L + 1):
+        q = lp[l:]
+        hi = np.minimum(l + q, Lw)
+        lo = q - l
+        hi = hi - ((hi - lo) % 2)
+        tot += int(np.sum(np.where(hi >= lo, (hi - lo) // 2 + 1, 0)))
+    return tot
+
+
+def coupling_measure(plan, wl, dev, L):
+    """The mode-coupling row (Sec. 2.1): W_l of the workload's randoms (scaled
+    by alpha) up to lmax, then M_ll' (Eq. chat) for 0 <= l, l' <= lmax, timed
+    with CUDA events (one warm-up, three timed calls).  FP64 pipe bound: per
+    term one multiply and one FMA = 3 flops."""
+    import torch
+
+    from paper_2312_12285_gb300 import ops
+    rnd = [c for c in wl.catalogs if c.name == "randoms"]
+    if not rnd:
+        return None
+    c = rnd[0]
+    cat = ops.Cat(torch.from_numpy(c.x).to(dev), torch.from_numpy(c.phi).to(dev), torch.from_numpy(c.w).to(dev), 0,
+                  abs(c.coeff))
+    W = ops.window_cl(plan, [cat], "fp32", subtract_noise=True)
+    M = ops.coupling(W, L)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        ops.coupling(W, L)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1) / 3
+    terms = coupling_terms(L, L)
+    ach = 3.0 * terms / (ms / 1e3) / 1e12
+    return {"value": terms / (ms / 1e3), "unit": "3j terms/s", "ms": ms, "terms": terms, "lmax": L, "lmax_w": L,
+            "finite": bool(torch.isfinite(M).all()),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                         "frac": ach / FP64_TFLOPS_NOMINAL,
+                         "kernel": "cp_coupling_kernel (FP64: one multiply + one FMA per term)",
+                         "peak_source": "nominal FP64 1.25 TFLOP/s"},
+            "what": "M_ll' (Eq. chat) from the randoms' window spectrum, lmax = lmax_w = workload lmax"}
 
 
 def adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src):

@@ -268,6 +268,62 @@ pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsht_catalog* 
                                     int32_t nfield, int32_t ntheta, double* alm_out, void* workspace,
                                     size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Mode coupling of the masked pseudo-spectrum (Sec. 2.1).
+ *
+ * The window's spectrum W_l (Eq. wldef) is the pseudo-C_l of the scaled
+ * randoms: pointsht_alm on the randoms with coeff = alpha, then pointsht_cl
+ * (with their shot noise alpha^2 sum w^2 / 4pi as `noise` when few randoms
+ * estimate the window).  The functions below take W_l on the device.
+ * All pointers are device pointers unless noted; everything is enqueued on
+ * `stream`; only argument errors are returned synchronously.
+ * ------------------------------------------------------------------- */
+
+/* Workspace of pointsht_coupling: two FP64 tables of 2 lmax + 1 entries. */
+size_t pointsht_workspace_size_coupling(int32_t lmax);
+
+/* M_ll' = (2l'+1)/(4 pi) sum_lambda (2 lambda+1) (l l' lambda; 0 0 0)^2 W_lambda
+ * (Eq. chat) for 0 <= l, l' <= lmax, lambda <= min(l + l', lmax_w); W_lambda
+ * beyond lmax_w counts as zero.  The 3j symbols with zero orders are those of
+ * App. "Wigner 3j symbols", evaluated through their closed form squared.
+ * W: lmax_w + 1 doubles; M: (lmax+1)^2 doubles, row-major M[l][l'],
+ * overwritten; workspace: >= pointsht_workspace_size_coupling(lmax) bytes,
+ * 256-byte aligned, clobbered.  0 <= lmax <= 8192.  FP64 throughout; work
+ * ~lmax^2 min(lmax, lmax_w)/6 terms.  Deterministic. */
+pointsht_status pointsht_coupling(int32_t lmax, int32_t lmax_w, const double* W, double* M,
+                                  void* workspace, size_t ws_bytes, void* stream);
+
+/* Binned coupling (Sec. 2.1, theta_b^l = 1/Delta_l on [edges[b], edges[b+1])):
+ * R[b][l'] = sum_l theta_b^l M_ll' (nbin x (lmax+1)) and
+ * M_bb' = sum_{l' in b'} R[b][l'] (nbin x nbin), the coupling between binned
+ * C^ and a true C_l that is constant on each bin.  edges: nbin + 1 int32
+ * (clamped into [0, lmax+1] on the device); 1 <= nbin <= 512. */
+pointsht_status pointsht_coupling_binned(int32_t lmax, const double* M, const int32_t* edges, int32_t nbin,
+                                         double* R, double* Mbb, void* stream);
+
+/* Workspace of pointsht_decouple: the augmented nbin x 2 nbin matrix. */
+size_t pointsht_workspace_size_decouple(int32_t nbin);
+
+/* Mode decoupling (Eq. mode_coupling, Eq. expectation_value): Minv = M_bb'^-1
+ * (Gauss-Jordan, partial pivoting, FP64; a singular matrix gives NaN
+ * everywhere in Minv and in what is computed from it), and optionally the
+ * window matrix Mcal[b][l'] = sum_b' Minv[b][b'] R[b'][l'] (R and Mcal both
+ * given or both NULL) and the decoupled bandpowers
+ * cl_dec[s][b] = sum_b' Minv[b][b'] cl_binned[s][b'] for nspec spectra
+ * (cl_binned and cl_dec both given or both NULL).  workspace: >=
+ * pointsht_workspace_size_decouple(nbin) bytes, 256-byte aligned. */
+pointsht_status pointsht_decouple(int32_t lmax, int32_t nbin, const double* Mbb, const double* R,
+                                  const double* cl_binned, int32_t nspec, double* Minv, double* Mcal,
+                                  double* cl_dec, void* workspace, size_t ws_bytes, void* stream);
+
+/* FKP-like normalisation (Sec. 2.1): norm[0] = 1 / [sum_l (2l+1) W_l / 4pi]
+ * over l <= lmax_w (it leaves the amplitude of a shot-noise spectrum
+ * unchanged), and optionally Mprime = norm R (nbin x (lmax+1)) and
+ * cl_norm = norm cl_binned (nspec x nbin); pairs both given or both NULL. */
+pointsht_status pointsht_fkp_normalise(int32_t lmax_w, const double* W, int32_t lmax, int32_t nbin,
+                                       const double* R, const double* cl_binned, int32_t nspec,
+                                       double* norm, double* Mprime, double* cl_norm, void* stream);
+
 /* Size of the fixed scratch array used by pointsht_alm_noalloc (64 MiB). */
 #define POINTSHT_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 

@@ -27,6 +27,8 @@ EXPORTS = (
     "pointsht_bin_backward", "pointsht_alm_backward", "pointsht_alm_noalloc",
     "pointsht_workspace_size_columns", "pointsht_alm_columns",
     "pointsht_workspace_size_interp", "pointsht_alm_interp",
+    "pointsht_workspace_size_coupling", "pointsht_coupling", "pointsht_coupling_binned",
+    "pointsht_workspace_size_decouple", "pointsht_decouple", "pointsht_fkp_normalise",
 )
 
 
@@ -82,6 +84,12 @@ def load(build_if_missing: bool = True):
             "pointsht_alm_columns": ([vp, vp, vp, vp, i64, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_workspace_size_interp": ([vp, cp, i32, i32, i32], sz),
             "pointsht_alm_interp": ([vp, cp, i32, i32, i32, dp, vp, sz, vp], ctypes.c_int),
+            "pointsht_workspace_size_coupling": ([i32], sz),
+            "pointsht_coupling": ([i32, i32, dp, dp, vp, sz, vp], ctypes.c_int),
+            "pointsht_coupling_binned": ([i32, dp, vp, i32, dp, dp, vp], ctypes.c_int),
+            "pointsht_workspace_size_decouple": ([i32], sz),
+            "pointsht_decouple": ([i32, i32, dp, dp, dp, i32, dp, dp, dp, vp, sz, vp], ctypes.c_int),
+            "pointsht_fkp_normalise": ([i32, dp, i32, i32, dp, dp, i32, dp, dp, dp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

@@ -36,6 +36,14 @@ cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
 int adjoint_sorted_points_per_warp();
+size_t coupling_smem_bytes(int);
+cudaError_t launch_coupling(int, int, const double*, double*, double*, double*, cudaStream_t);
+cudaError_t launch_coupling_binned(int, const double*, const int*, int, double*, double*, cudaStream_t);
+size_t decouple_workspace_bytes(int);
+cudaError_t launch_decouple(int, int, const double*, const double*, const double*, int, double*, double*, double*,
+                            double*, cudaStream_t);
+cudaError_t launch_fkp_normalise(int, const double*, int, int, const double*, const double*, int, double*, double*,
+                                 double*, cudaStream_t);
 cudaError_t launch_adjoint_sorted(const AdjointParams&, const double*, const double*, cudaStream_t);
 cudaError_t launch_sort_offsets_f32(const SortParams&, cudaStream_t);
 size_t mixed_smem_bytes(int);
@@ -1118,5 +1126,81 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
     ap.alpha = plan->alpha_d;
     e = launch_adjoint(lo.is_f64, ap, st);
     if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+// ------------------------------------------------------- mode coupling --
+static const int COUPLING_MAX_LMAX = 8192;
+static const int DECOUPLE_MAX_NBIN = 512;
+
+extern "C" size_t pointsht_workspace_size_coupling(int32_t lmax) {
+    if (lmax < 0 || lmax > COUPLING_MAX_LMAX) return 0;
+    return up256((size_t)(2 * lmax + 1) * 8) * 2;
+}
+
+extern "C" pointsht_status pointsht_coupling(int32_t lmax, int32_t lmax_w, const double* W, double* M,
+                                             void* workspace, size_t ws_bytes, void* stream) {
+    if (lmax < 0 || lmax > COUPLING_MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "coupling: lmax=%d outside [0, %d]", lmax, COUPLING_MAX_LMAX);
+    if (lmax_w < 0) return fail(POINTSHT_EINVAL, "coupling: lmax_w=%d < 0", lmax_w);
+    if (!W || !M || !workspace) return fail(POINTSHT_EINVAL, "coupling: NULL pointer");
+    if (((uintptr_t)W | (uintptr_t)M) % 8) return fail(POINTSHT_EINVAL, "coupling: W or M not 8-byte aligned");
+    const size_t need = pointsht_workspace_size_coupling(lmax);
+    if (ws_bytes < need || ((uintptr_t)workspace % 256))
+        return fail(POINTSHT_EINVAL, "coupling: workspace of %zu bytes (need %zu, 256-byte aligned)", ws_bytes, need);
+    // W beyond 2 lmax never enters (lambda <= l + l')
+    const int lw = std::min(lmax_w, 2 * lmax);
+    double* b = static_cast<double*>(workspace);
+    double* ib = reinterpret_cast<double*>(static_cast<char*>(workspace) + need / 2);
+    cudaError_t e = launch_coupling(lmax, lw, W, M, b, ib, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "coupling: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_coupling_binned(int32_t lmax, const double* M, const int32_t* edges, int32_t nbin,
+                                                    double* R, double* Mbb, void* stream) {
+    if (lmax < 0 || nbin < 1 || nbin > DECOUPLE_MAX_NBIN)
+        return fail(POINTSHT_EINVAL, "coupling_binned: lmax=%d, nbin=%d (1..%d)", lmax, nbin, DECOUPLE_MAX_NBIN);
+    if (!M || !edges || !R || !Mbb) return fail(POINTSHT_EINVAL, "coupling_binned: NULL pointer");
+    cudaError_t e = launch_coupling_binned(lmax, M, edges, nbin, R, Mbb, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "coupling_binned: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" size_t pointsht_workspace_size_decouple(int32_t nbin) {
+    if (nbin < 1 || nbin > DECOUPLE_MAX_NBIN) return 0;
+    return up256(decouple_workspace_bytes(nbin));
+}
+
+extern "C" pointsht_status pointsht_decouple(int32_t lmax, int32_t nbin, const double* Mbb, const double* R,
+                                             const double* cl_binned, int32_t nspec, double* Minv, double* Mcal,
+                                             double* cl_dec, void* workspace, size_t ws_bytes, void* stream) {
+    if (lmax < 0 || nbin < 1 || nbin > DECOUPLE_MAX_NBIN || nspec < 0)
+        return fail(POINTSHT_EINVAL, "decouple: lmax=%d, nbin=%d (1..%d), nspec=%d", lmax, nbin, DECOUPLE_MAX_NBIN,
+                    nspec);
+    if (!Mbb || !Minv || !workspace) return fail(POINTSHT_EINVAL, "decouple: NULL pointer");
+    if ((!R) != (!Mcal)) return fail(POINTSHT_EINVAL, "decouple: R and Mcal must be given together");
+    if ((!cl_binned) != (!cl_dec)) return fail(POINTSHT_EINVAL, "decouple: cl_binned and cl_dec must be given together");
+    const size_t need = pointsht_workspace_size_decouple(nbin);
+    if (ws_bytes < need || ((uintptr_t)workspace % 256))
+        return fail(POINTSHT_EINVAL, "decouple: workspace of %zu bytes (need %zu, 256-byte aligned)", ws_bytes, need);
+    cudaError_t e = launch_decouple(lmax, nbin, Mbb, R, cl_binned, nspec, Minv, Mcal, cl_dec,
+                                    static_cast<double*>(workspace), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "decouple: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_fkp_normalise(int32_t lmax_w, const double* W, int32_t lmax, int32_t nbin,
+                                                  const double* R, const double* cl_binned, int32_t nspec,
+                                                  double* norm, double* Mprime, double* cl_norm, void* stream) {
+    if (lmax_w < 0 || !W || !norm) return fail(POINTSHT_EINVAL, "fkp_normalise: lmax_w=%d, W or norm NULL", lmax_w);
+    if ((!R) != (!Mprime)) return fail(POINTSHT_EINVAL, "fkp_normalise: R and Mprime must be given together");
+    if ((!cl_binned) != (!cl_norm))
+        return fail(POINTSHT_EINVAL, "fkp_normalise: cl_binned and cl_norm must be given together");
+    if ((R || cl_binned) && (nbin < 1 || lmax < 0 || nspec < 0))
+        return fail(POINTSHT_EINVAL, "fkp_normalise: lmax=%d, nbin=%d, nspec=%d", lmax, nbin, nspec);
+    cudaError_t e = launch_fkp_normalise(lmax_w, W, lmax, nbin, R, cl_binned, nspec, norm, Mprime, cl_norm,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "fkp_normalise: %s", cudaGetErrorString(e));
     return POINTSHT_OK;
 }

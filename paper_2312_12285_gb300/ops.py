@@ -261,6 +261,109 @@ def bin_backward_raw(grad_b, edges, lmax, stream=None):
     return out
 
 
+# ------------------------------------------------------- mode coupling --
+def _f64_dev(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    return t.contiguous()
+
+
+def window_cl(plan: Plan, randoms, precision: str = "fp32", subtract_noise: bool = False, workspace=None,
+              stream=None):
+    """W_l (Eq. wldef) of the window traced by the scaled randoms (their Cat
+    coeff = alpha): pointsht_alm on the randoms alone, then pointsht_cl, with
+    their shot noise alpha^2 sum w^2 / 4pi subtracted if asked (for a window
+    estimated from few randoms)."""
+    cats = [Cat(c.x, c.phi, c.w, 0, c.coeff) for c in randoms]
+    a = alm_raw(plan, cats, 1, precision, workspace=workspace, stream=stream)
+    noise = shot_noise_raw(cats, 1, precision, a.device, stream=stream) if subtract_noise else None
+    return cl_raw(a, noise, stream=stream)[0]
+
+
+def coupling(W: torch.Tensor, lmax: int, workspace=None, stream=None) -> torch.Tensor:
+    """M_ll' of Eq. chat, (lmax+1, lmax+1) float64, from W_0..W_{lmax_w}
+    (pointsht_coupling)."""
+    lib = _lib.load()
+    W = _f64_dev(W, "W")
+    need = lib.pointsht_workspace_size_coupling(int(lmax))
+    if need == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_coupling")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=W.device)
+    M = torch.empty((lmax + 1, lmax + 1), dtype=torch.float64, device=W.device)
+    _lib.check(lib.pointsht_coupling(int(lmax), W.shape[0] - 1, _ptr(W), _ptr(M), _ptr(workspace), workspace.numel(),
+                                     _stream_ptr(stream)), "coupling")
+    return M
+
+
+def coupling_binned(M: torch.Tensor, edges: torch.Tensor, stream=None):
+    """(R, M_bb'): R[b, l'] = sum_l theta_b^l M_ll', M_bb' = sum_{l' in b'} R[b, l']
+    (pointsht_coupling_binned)."""
+    lib = _lib.load()
+    M = _f64_dev(M, "M")
+    L = M.shape[0] - 1
+    nbin = edges.shape[0] - 1
+    R = torch.empty((nbin, L + 1), dtype=torch.float64, device=M.device)
+    Mbb = torch.empty((nbin, nbin), dtype=torch.float64, device=M.device)
+    _lib.check(lib.pointsht_coupling_binned(L, _ptr(M), _ptr(edges.contiguous()), nbin, _ptr(R), _ptr(Mbb),
+                                            _stream_ptr(stream)), "coupling_binned")
+    return R, Mbb
+
+
+def decouple(Mbb: torch.Tensor, R=None, cl_binned=None, stream=None):
+    """(Minv, Mcal, cl_dec) of Eq. mode_coupling / Eq. expectation_value
+    (pointsht_decouple); Mcal / cl_dec are None when R / cl_binned are."""
+    lib = _lib.load()
+    Mbb = _f64_dev(Mbb, "Mbb")
+    nbin = Mbb.shape[0]
+    dev = Mbb.device
+    L = R.shape[1] - 1 if R is not None else 0
+    need = lib.pointsht_workspace_size_decouple(nbin)
+    if need == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_decouple")
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    Minv = torch.empty((nbin, nbin), dtype=torch.float64, device=dev)
+    Mcal = torch.empty((nbin, L + 1), dtype=torch.float64, device=dev) if R is not None else None
+    if R is not None:
+        R = _f64_dev(R, "R")
+    nspec = 0
+    cl_dec = None
+    if cl_binned is not None:
+        cl_binned = _f64_dev(cl_binned, "cl_binned")
+        nspec = cl_binned.shape[0]
+        cl_dec = torch.empty((nspec, nbin), dtype=torch.float64, device=dev)
+    _lib.check(lib.pointsht_decouple(L, nbin, _ptr(Mbb), _ptr(R) if R is not None else None,
+                                     _ptr(cl_binned) if cl_binned is not None else None, nspec, _ptr(Minv),
+                                     _ptr(Mcal) if Mcal is not None else None,
+                                     _ptr(cl_dec) if cl_dec is not None else None, _ptr(ws), ws.numel(),
+                                     _stream_ptr(stream)), "decouple")
+    return Minv, Mcal, cl_dec
+
+
+def fkp_normalise(W: torch.Tensor, R=None, cl_binned=None, stream=None):
+    """(norm, Mprime, cl_norm): norm = 1 / [sum_l (2l+1) W_l / 4pi], Mprime =
+    norm R, cl_norm = norm cl_binned (pointsht_fkp_normalise)."""
+    lib = _lib.load()
+    W = _f64_dev(W, "W")
+    dev = W.device
+    norm = torch.empty(1, dtype=torch.float64, device=dev)
+    L, nbin, nspec = 0, 0, 0
+    Mp = cn = None
+    if R is not None:
+        R = _f64_dev(R, "R")
+        nbin, L = R.shape[0], R.shape[1] - 1
+        Mp = torch.empty_like(R)
+    if cl_binned is not None:
+        cl_binned = _f64_dev(cl_binned, "cl_binned")
+        nspec, nbin = cl_binned.shape
+        cn = torch.empty_like(cl_binned)
+    _lib.check(lib.pointsht_fkp_normalise(W.shape[0] - 1, _ptr(W), L, nbin, _ptr(R) if R is not None else None,
+                                          _ptr(cl_binned) if cl_binned is not None else None, nspec, _ptr(norm),
+                                          _ptr(Mp) if Mp is not None else None, _ptr(cn) if cn is not None else None,
+                                          _stream_ptr(stream)), "fkp_normalise")
+    return norm, Mp, cn
+
+
 def combine_raw(alm_src, coef, noise_src=None, stream=None):
     """Linear combination of fields (pointsht_combine)."""
     lib = _lib.load()
