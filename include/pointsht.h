@@ -268,6 +268,26 @@ pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsht_catalog* 
                                     int32_t nfield, int32_t ntheta, double* alm_out, void* workspace,
                                     size_t ws_bytes, void* stream);
 
+/* Point-evaluation synthesis: out[i] = sum_{l <= lmax, |m| <= l} a_lm Y_lm(theta_i, phi_i)
+ * for the real field whose m >= 0 coefficients are `alm` (a_{l,-m} =
+ * (-1)^m conj(a_lm), Condon-Shortley phase), i.e.
+ * sum_l [a_l0 Y_l0 + 2 sum_{m>0} Re(a_lm Y_lm)].  This is the operation the
+ * paper names for releasing or apodising the a_lm as a band-limited function
+ * (Sec. "Conclusions"; Eq. alm_def read backwards), and the transpose of the
+ * analysis: it runs the adjoint kernels with unit weights.
+ * x = cos(theta), phi: device, n values of float (POINTSHT_FP32) or double
+ * (POINTSHT_FP64); alm: device, M complex128 (the packed m-major triangle of
+ * the plan's lmax); out: device, n values of the input type, overwritten;
+ * workspace: >= pointsht_workspace_size_synthesis() bytes, 256-byte aligned,
+ * clobbered.  |x| > 1 or non-finite inputs raise ERANGE at the next
+ * pointsht_plan_check (those points get the value at x = 0, phi = 0).  FP32:
+ * lmax <= the FP32 path's limit and n < 2^32 - 1. */
+size_t pointsht_workspace_size_synthesis(pointsht_plan plan, int64_t n, pointsht_precision prec);
+
+pointsht_status pointsht_synthesis(pointsht_plan plan, const void* x, const void* phi, int64_t n,
+                                   pointsht_precision prec, const double* alm, void* out, void* workspace,
+                                   size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------------
  * Mode coupling of the masked pseudo-spectrum (Sec. 2.1).
  *

@@ -57,6 +57,8 @@ def _load():
             lib.oracle_alm.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_synthesis.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+            lib.oracle_synthesis.restype = ctypes.c_int
             lib.oracle_threej000.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_threej000.restype = ctypes.c_double
             lib.oracle_coupling.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
@@ -281,6 +283,26 @@ def alm_interp(x, phi, w, lmax: int, ntheta: int, nthreads: int = 0):
     if rc != 0:
         raise RuntimeError(f"oracle_alm_interp failed ({rc})")
     return out[0::2] + 1j * out[1::2]
+
+
+# ------------------------------------------------ point-evaluation synthesis --
+def synthesis(x, phi, alm_t, lmax: int, return_imag: bool = False, nthreads: int = 0):
+    """f(n_i) = sum_l sum_{m=-l}^{l} a_lm Y_lm(n_i) of the real field with
+    m >= 0 coefficients alm_t (packed triangle), negative orders written out
+    from a_{l,-m} = (-1)^m conj(a_lm), Y_{l,-m} = (-1)^m conj(Y_lm)."""
+    lib = _load()
+    x, phi = _f64(x), _f64(phi)
+    a = np.ascontiguousarray(np.asarray(alm_t, np.complex128))
+    assert a.shape[0] == nmodes(lmax)
+    ai = np.empty(2 * a.shape[0], np.float64)
+    ai[0::2], ai[1::2] = a.real, a.imag
+    re = np.zeros(x.shape[0], np.float64)
+    im = np.zeros(x.shape[0], np.float64)
+    rc = lib.oracle_synthesis(x.shape[0], _dptr(x), _dptr(phi), int(lmax), _dptr(ai), _dptr(re), _dptr(im),
+                              int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_synthesis failed ({rc})")
+    return (re, im) if return_imag else re
 
 
 # ------------------------------------- Eq. wldef, Eq. chat, mode decoupling --

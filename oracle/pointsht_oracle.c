@@ -520,3 +520,62 @@ int oracle_coupling_row(int lmax, int lmax_w, const double* W, int l, double* ro
     free(lf);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Point-evaluation synthesis: f(n_i) = sum_{l} sum_{m=-l}^{l} a_lm Y_lm(n_i)
+ * of a real field given by its m >= 0 coefficients, with the negative orders
+ * written out from a_{l,-m} = (-1)^m conj(a_lm) and
+ * Y_{l,-m} = (-1)^m conj(Y_lm) (App. A's Y_lm, Condon-Shortley phase).
+ * out_re gets the real part; out_im (optional) the imaginary part, which is
+ * zero for a real field up to rounding.
+ * ---------------------------------------------------------------------- */
+int oracle_synthesis(int64_t n, const double* x, const double* phi, int lmax, const double* a, double* out_re,
+                     double* out_im, int nthreads) {
+    if (n < 0 || lmax < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int status = 0;
+#pragma omp parallel
+    {
+        double* c1 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* c2 = (double*)calloc((size_t)lmax + 1, sizeof(double));
+        double* mant = (double*)malloc(sizeof(double) * ((size_t)lmax + 1));
+        int* expo = (int*)malloc(sizeof(int) * ((size_t)lmax + 1));
+        if (!c1 || !c2 || !mant || !expo) {
+#pragma omp critical
+            status = -2;
+        } else {
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t i = 0; i < n; ++i) {
+                nsum re = {0.0, 0.0}, im = {0.0, 0.0};
+                for (int m = 0; m <= lmax; ++m) {
+                    pbar_coeffs(lmax, m, c1, c2);
+                    pbar_column_scaled(x[i], lmax, m, c1, c2, mant, expo);
+                    const double c = cos((double)m * phi[i]), s = sin((double)m * phi[i]);
+                    const int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+                    const double sg = (m & 1) ? -1.0 : 1.0;
+                    for (int l = m; l <= lmax; ++l) {
+                        const double lam = sqrt((2.0 * l + 1.0) / (4.0 * ORACLE_PI)) * ldexp(mant[l - m], expo[l - m]);
+                        const double yr = lam * c, yi = lam * s;       /* Y_lm */
+                        const double ar = a[2 * (base + l)], ai = a[2 * (base + l) + 1];
+                        nsum_add(&re, ar * yr - ai * yi);               /* a_lm Y_lm */
+                        nsum_add(&im, ar * yi + ai * yr);
+                        if (m > 0) {                                    /* a_{l,-m} Y_{l,-m} */
+                            const double br = sg * ar, bi = -sg * ai;   /* (-1)^m conj(a_lm) */
+                            const double zr = sg * yr, zi = -sg * yi;   /* (-1)^m conj(Y_lm) */
+                            nsum_add(&re, br * zr - bi * zi);
+                            nsum_add(&im, br * zi + bi * zr);
+                        }
+                    }
+                }
+                out_re[i] = nsum_val(&re);
+                if (out_im) out_im[i] = nsum_val(&im);
+            }
+        }
+        free(c1); free(c2); free(mant); free(expo);
+    }
+    return status;
+}

@@ -27,6 +27,7 @@ EXPORTS = (
     "pointsht_bin_backward", "pointsht_alm_backward", "pointsht_alm_noalloc",
     "pointsht_workspace_size_columns", "pointsht_alm_columns",
     "pointsht_workspace_size_interp", "pointsht_alm_interp",
+    "pointsht_workspace_size_synthesis", "pointsht_synthesis",
     "pointsht_workspace_size_coupling", "pointsht_coupling", "pointsht_coupling_binned",
     "pointsht_workspace_size_decouple", "pointsht_decouple", "pointsht_fkp_normalise",
 )
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = True):
             "pointsht_alm_columns": ([vp, vp, vp, vp, i64, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_workspace_size_interp": ([vp, cp, i32, i32, i32], sz),
             "pointsht_alm_interp": ([vp, cp, i32, i32, i32, dp, vp, sz, vp], ctypes.c_int),
+            "pointsht_workspace_size_synthesis": ([vp, i64, ctypes.c_int], sz),
+            "pointsht_synthesis": ([vp, vp, vp, i64, ctypes.c_int, dp, vp, vp, sz, vp], ctypes.c_int),
             "pointsht_workspace_size_coupling": ([i32], sz),
             "pointsht_coupling": ([i32, i32, dp, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_coupling_binned": ([i32, dp, vp, i32, dp, dp, vp], ctypes.c_int),

@@ -320,6 +320,16 @@ def log_bin_edges(lmax: int, nbins: int = 32) -> np.ndarray:
     return np.asarray(e, np.int64)
 
 
+def golden_spiral_workload(n: int = 163_840, lmax: int = 2048, jitter: float = 1e-6, config_id: int = 6,
+                           dtype=np.float32) -> Workload:
+    """The golden-spiral example (Sec. 3.1) as a workload: ``golden_spiral``
+    points with w = 1 in one field.  A blue spectrum: most of its power at
+    high l."""
+    x, phi = golden_spiral(n, rng_for(config_id), jitter, dtype)
+    cats = [Catalog(x, phi, np.ones(n, dtype), 1.0, 0, "spiral")]
+    return Workload("golden_spiral", lmax, "fp32", 1, cats, {"jitter": jitter})
+
+
 def config(i: int, scale: float = 1.0, lmax: int | None = None) -> Workload:
     """The five configurations, optionally with point counts scaled by ``scale``.
 
@@ -328,6 +338,7 @@ def config(i: int, scale: float = 1.0, lmax: int | None = None) -> Workload:
     3 precision: 1e7 points (1e6 galaxies + 9e6 randoms), same mask/field, lmax 2048.
     4 batching: 16 bins of 10^U[5,7] galaxies + 2e7 shared randoms, lmax 1536.
     5 differentiation: 2e6 galaxies + 1e7 randoms, lmax 1024, 32 log bins.
+    6 golden spiral: 163 840 points with |cos theta| <= 1/2, w = 1, lmax 2048.
     """
     def sc(n):
         return max(1, int(round(n * scale)))
@@ -352,4 +363,6 @@ def config(i: int, scale: float = 1.0, lmax: int | None = None) -> Workload:
         wl.extra["fd_idx"] = [np.sort(r.choice(ng, min(32, ng), replace=False)),
                               np.sort(r.choice(nr, min(32, nr), replace=False))]
         return wl
+    if i == 6:
+        return golden_spiral_workload(sc(163_840), lmax or 2048)
     raise ValueError(f"unknown config {i}")

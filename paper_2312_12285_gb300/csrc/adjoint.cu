@@ -15,6 +15,8 @@
 
 #include <math_constants.h>
 
+#include <algorithm>
+
 namespace psht {
 
 // Seed, phase and coefficient loads for the adjoint, from per-point values
@@ -412,8 +414,10 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
 
 // gtab entries for the sorted FP32 adjoint: (gamma g re, same, gamma g im, same)
 __global__ void build_gtab4_kernel(int L, const double2* __restrict__ galm, const double* __restrict__ gamma,
-                                   const int64_t* __restrict__ colstart, int64_t gstride, float4* __restrict__ gtab) {
+                                   const int64_t* __restrict__ colstart, int64_t gstride, int synth,
+                                   float4* __restrict__ gtab) {
     const int m = blockIdx.y, f = blockIdx.z;
+    const double cm = (synth && m > 0) ? 2.0 : 1.0;
     const int64_t w = colstart[m + 1] - colstart[m];
     const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < w; q += (int64_t)gridDim.x * blockDim.x) {
@@ -421,7 +425,7 @@ __global__ void build_gtab4_kernel(int L, const double2* __restrict__ galm, cons
         if (m + q <= L) {
             const int64_t idx = tri_base(m, L) + m + q;
             const double2 g = galm[(int64_t)f * M + idx];
-            const double gm = gamma[idx];
+            const double gm = cm * gamma[idx];
             v = make_float4((float)(g.x * gm), (float)(g.x * gm), (float)(g.y * gm), (float)(g.y * gm));
         }
         gtab[(int64_t)f * gstride + colstart[m] + q] = v;
@@ -430,11 +434,11 @@ __global__ void build_gtab4_kernel(int L, const double2* __restrict__ galm, cons
 
 int adjoint_sorted_points_per_warp() { return ADJ_PW; }
 
-cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, const double* gamma,
+cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, const double* gamma, int synth,
                                   cudaStream_t st) {
     dim3 grid(4, ap.lmax + 1, ap.nfield);
     build_gtab4_kernel<<<grid, 256, 0, st>>>(ap.lmax, reinterpret_cast<const double2*>(galm), gamma, ap.colstart,
-                                             ap.gstride, (float4*)ap.gtab);
+                                             ap.gstride, synth, (float4*)ap.gtab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t nwarps = ap.ntot / ADJ_PW;
@@ -443,11 +447,16 @@ cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, c
     return cudaGetLastError();
 }
 
-// gtab[f][colstart[m] + q] = gamma(l, m) * g^f(l, m), zero in the padding.
+// gtab[f][colstart[m] + q] = c_m gamma(l, m) * g^f(l, m), zero in the padding;
+// c_m = 1, or for point-evaluation synthesis (the real field
+// sum_{l, |m| <= l} a_lm Y_lm = sum_l [a_l0 Y_l0 + 2 sum_{m>0} Re(a_lm Y_lm)])
+// c_m = 2 for m > 0.
 template <typename R2>
 __global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const double* __restrict__ gamma,
-                                  const int64_t* __restrict__ colstart, int64_t gstride, R2* __restrict__ gtab) {
+                                  const int64_t* __restrict__ colstart, int64_t gstride, int synth,
+                                  R2* __restrict__ gtab) {
     const int m = blockIdx.y, f = blockIdx.z;
+    const double cm = (synth && m > 0) ? 2.0 : 1.0;
     const int64_t w = colstart[m + 1] - colstart[m];
     const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < w; q += (int64_t)gridDim.x * blockDim.x) {
@@ -457,7 +466,7 @@ __global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const
         if (m + q <= L) {
             const int64_t idx = tri_base(m, L) + m + q;
             const double2 g = galm[(int64_t)f * M + idx];
-            const double gm = gamma[idx];
+            const double gm = cm * gamma[idx];
             v.x = g.x * gm;
             v.y = g.y * gm;
         }
@@ -466,14 +475,14 @@ __global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const
 }
 
 cudaError_t launch_build_gtab(int is_f64, int L, int nfield, const double* galm, const double* gamma,
-                              const int64_t* colstart, int64_t gstride, void* gtab, cudaStream_t st) {
+                              const int64_t* colstart, int64_t gstride, int synth, void* gtab, cudaStream_t st) {
     dim3 grid(4, L + 1, nfield);
     if (is_f64)
         build_gtab_kernel<double2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
-                                                         gstride, static_cast<double2*>(gtab));
+                                                         gstride, synth, static_cast<double2*>(gtab));
     else
         build_gtab_kernel<float2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
-                                                        gstride, static_cast<float2*>(gtab));
+                                                        gstride, synth, static_cast<float2*>(gtab));
     return cudaGetLastError();
 }
 
@@ -488,4 +497,22 @@ cudaError_t launch_adjoint(int is_f64, const AdjointParams& ap, cudaStream_t st)
     return cudaGetLastError();
 }
 
+}  // namespace psht
+
+namespace psht {
+// Unit weights for point-evaluation synthesis (the catalog form needs a
+// weight array; synthesis has none).
+__global__ void fill_ones_kernel(int64_t n, int is_f64, void* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (is_f64) static_cast<double*>(out)[i] = 1.0;
+        else static_cast<float*>(out)[i] = 1.0f;
+    }
+}
+
+cudaError_t launch_fill_ones(int64_t n, int is_f64, void* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    fill_ones_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, is_f64, out);
+    return cudaGetLastError();
+}
 }  // namespace psht

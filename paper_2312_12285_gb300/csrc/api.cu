@@ -31,7 +31,7 @@ cudaError_t launch_bin_backward(int, const double*, int, const int*, int, double
 cudaError_t launch_combine(int, const double*, int, const double*, int, const double*, double*, double*,
                            cudaStream_t);
 cudaError_t launch_shot_noise(const PrepParams&, int, double*, int, double*, cudaStream_t);
-cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const int64_t*, int64_t, void*,
+cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const int64_t*, int64_t, int, void*,
                               cudaStream_t);
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
@@ -44,7 +44,8 @@ cudaError_t launch_decouple(int, int, const double*, const double*, const double
                             double*, cudaStream_t);
 cudaError_t launch_fkp_normalise(int, const double*, int, int, const double*, const double*, int, double*, double*,
                                  double*, cudaStream_t);
-cudaError_t launch_adjoint_sorted(const AdjointParams&, const double*, const double*, cudaStream_t);
+cudaError_t launch_adjoint_sorted(const AdjointParams&, const double*, const double*, int, cudaStream_t);
+cudaError_t launch_fill_ones(int64_t, int, void*, cudaStream_t);
 cudaError_t launch_sort_offsets_f32(const SortParams&, cudaStream_t);
 size_t mixed_smem_bytes(int);
 int mixed_tile_points();
@@ -1036,25 +1037,12 @@ extern "C" pointsht_status pointsht_bin_backward(int32_t lmax, const double* gra
 }
 
 // --------------------------------------------------------- adjoint --
-extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
-                                                 int32_t nfield, pointsht_precision prec, const double* grad_alm,
-                                                 const double* grad_noise, void* const* grad_w, void* workspace,
-                                                 size_t ws_bytes, void* stream) {
-    pointsht_status s = check_common(plan, cats, ncat, nfield, prec, "alm_backward");
-    if (s != POINTSHT_OK) return s;
-    if (prec == POINTSHT_MIXED) prec = POINTSHT_FP32;  // the adjoint has no per-m contraction to move
-    if (!grad_alm || ((uintptr_t)grad_alm % 16)) return fail(POINTSHT_EINVAL, "alm_backward: grad_alm NULL/misaligned");
-    if (ncat > 0 && !grad_w) return fail(POINTSHT_EINVAL, "alm_backward: grad_w is NULL");
-    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
-    for (int c = 0; c < ncat; ++c)
-        if (cats[c].n > 0 && (!grad_w[c] || (uintptr_t)grad_w[c] % esz))
-            return fail(POINTSHT_EINVAL, "alm_backward: grad_w[%d] NULL or misaligned", c);
-    if ((s = check_device(plan, "alm_backward")) != POINTSHT_OK) return s;
-    Layout lo;
-    make_layout(plan, cats, ncat, nfield, prec, lo);
-    if ((s = check_ws(lo, workspace, ws_bytes, lo.total, "alm_backward")) != POINTSHT_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    char* ws = static_cast<char*>(workspace);
+// The point-evaluation kernels behind pointsht_alm_backward (synth = 0) and
+// pointsht_synthesis (synth = 1: table factor c_m, coeff 1, no noise term).
+// Arguments already checked; the layout is make_layout's for these catalogs.
+static pointsht_status run_adjoint(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat, int32_t nfield,
+                                   const Layout& lo, const double* grad_alm, const double* grad_noise,
+                                   void* const* grad_w, char* ws, int synth, cudaStream_t st, const char* who) {
     void* gtab = ws + lo.gtab_off;
     cudaError_t e;
     AdjointParams ap;
@@ -1076,7 +1064,7 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
         int64_t npts = 0;
         for (int c = 0; c < ncat; ++c) npts += cats[c].n;
         if (npts >= (int64_t)0xffffffffLL)
-            return fail(POINTSHT_EINVAL, "alm_backward: %lld points; the FP32 adjoint takes fewer than 2^32 - 1",
+            return fail(POINTSHT_EINVAL, "%s: %lld points; the FP32 path takes fewer than 2^32 - 1", who,
                         (long long)npts);
         PrepParams pp;
         fill_prep(cats, ncat, nfield, lo, ws + lo.pts_off, plan->err, pp);
@@ -1093,7 +1081,7 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
             for (int f = 0; f < nfield; ++f) sp.field_off[f] = lo.off[f];
             sp.hist = reinterpret_cast<int64_t*>(ws + lo.hist_off);
             e = launch_prep_sorted<float>(sp, st);
-            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: prep launch: %s", cudaGetErrorString(e));
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: prep launch: %s", who, cudaGetErrorString(e));
         }
         for (int c = 0; c < ncat; ++c) {
             ap.cat[c] = pp.cat[c];
@@ -1103,12 +1091,13 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
         ap.ntot = lo.ntot;
         for (int f = 0; f < nfield; ++f) ap.fld[f].off = lo.off[f];
         ap.alpha2 = plan->alpha_f2;
-        e = launch_adjoint_sorted(ap, grad_alm, plan->gamma, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
+        e = launch_adjoint_sorted(ap, grad_alm, plan->gamma, synth, st);
+        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: adjoint: %s", who, cudaGetErrorString(e));
         return POINTSHT_OK;
     }
-    e = launch_build_gtab(lo.is_f64, plan->lmax, nfield, grad_alm, plan->gamma, plan->colstart, plan->acol, gtab, st);
-    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: table: %s", cudaGetErrorString(e));
+    e = launch_build_gtab(lo.is_f64, plan->lmax, nfield, grad_alm, plan->gamma, plan->colstart, plan->acol, synth,
+                          gtab, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: table: %s", who, cudaGetErrorString(e));
     const int ppw = adjoint_points_per_warp(lo.is_f64);
     int64_t wsum = 0;
     for (int c = 0; c < ncat; ++c) {
@@ -1125,8 +1114,87 @@ extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const point
     ap.warp0[ncat] = wsum;
     ap.alpha = plan->alpha_d;
     e = launch_adjoint(lo.is_f64, ap, st);
-    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_backward: adjoint: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: adjoint: %s", who, cudaGetErrorString(e));
     return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
+                                                 int32_t nfield, pointsht_precision prec, const double* grad_alm,
+                                                 const double* grad_noise, void* const* grad_w, void* workspace,
+                                                 size_t ws_bytes, void* stream) {
+    pointsht_status s = check_common(plan, cats, ncat, nfield, prec, "alm_backward");
+    if (s != POINTSHT_OK) return s;
+    if (prec == POINTSHT_MIXED) prec = POINTSHT_FP32;  // the adjoint has no per-m contraction to move
+    if (!grad_alm || ((uintptr_t)grad_alm % 16)) return fail(POINTSHT_EINVAL, "alm_backward: grad_alm NULL/misaligned");
+    if (ncat > 0 && !grad_w) return fail(POINTSHT_EINVAL, "alm_backward: grad_w is NULL");
+    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
+    for (int c = 0; c < ncat; ++c)
+        if (cats[c].n > 0 && (!grad_w[c] || (uintptr_t)grad_w[c] % esz))
+            return fail(POINTSHT_EINVAL, "alm_backward: grad_w[%d] NULL or misaligned", c);
+    if (prec != POINTSHT_FP64 && plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "alm_backward: the FP32 path supports lmax <= %d (plan has %d)",
+                    F32Scale::MAX_LMAX, plan->lmax);
+    if ((s = check_device(plan, "alm_backward")) != POINTSHT_OK) return s;
+    Layout lo;
+    make_layout(plan, cats, ncat, nfield, prec, lo);
+    if ((s = check_ws(lo, workspace, ws_bytes, lo.total, "alm_backward")) != POINTSHT_OK) return s;
+    return run_adjoint(plan, cats, ncat, nfield, lo, grad_alm, grad_noise, grad_w, static_cast<char*>(workspace), 0,
+                       static_cast<cudaStream_t>(stream), "alm_backward");
+}
+
+// ------------------------------------------------------- synthesis --
+// The unit-weight catalog of a synthesis call: weights in the workspace
+// after the adjoint's own layout.
+static void synthesis_catalog(const void* x, const void* phi, int64_t n, pointsht_catalog& cat) {
+    memset(&cat, 0, sizeof(cat));
+    cat.x = x;
+    cat.phi = phi;
+    cat.w = nullptr;  // set to the workspace's ones once placed
+    cat.n = n;
+    cat.field = 0;
+    cat.coeff = 1.0;
+}
+
+extern "C" size_t pointsht_workspace_size_synthesis(pointsht_plan plan, int64_t n, pointsht_precision prec) {
+    if (!plan || n < 0 || (prec != POINTSHT_FP32 && prec != POINTSHT_FP64)) return 0;
+    pointsht_catalog cat;
+    synthesis_catalog(nullptr, nullptr, n, cat);
+    Layout lo;
+    if (make_layout(plan, &cat, 1, 1, prec, lo) != POINTSHT_OK) return 0;
+    return up256(lo.total) + up256((size_t)n * (prec == POINTSHT_FP64 ? 8 : 4));
+}
+
+extern "C" pointsht_status pointsht_synthesis(pointsht_plan plan, const void* x, const void* phi, int64_t n,
+                                              pointsht_precision prec, const double* alm, void* out, void* workspace,
+                                              size_t ws_bytes, void* stream) {
+    if (!plan) return fail(POINTSHT_EINVAL, "synthesis: plan is NULL");
+    if (prec != POINTSHT_FP32 && prec != POINTSHT_FP64)
+        return fail(POINTSHT_EINVAL, "synthesis: precision must be POINTSHT_FP32 or POINTSHT_FP64");
+    if (n < 0) return fail(POINTSHT_EINVAL, "synthesis: n=%lld < 0", (long long)n);
+    const size_t esz = prec == POINTSHT_FP64 ? 8 : 4;
+    if (!alm || ((uintptr_t)alm % 16)) return fail(POINTSHT_EINVAL, "synthesis: alm NULL or not 16-byte aligned");
+    if (n > 0 && (!x || !phi || !out || (((uintptr_t)x | (uintptr_t)phi | (uintptr_t)out) % esz)))
+        return fail(POINTSHT_EINVAL, "synthesis: x, phi or out NULL or not %zu-byte aligned", esz);
+    if (prec == POINTSHT_FP32 && plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "synthesis: the FP32 path supports lmax <= %d (plan has %d)", F32Scale::MAX_LMAX,
+                    plan->lmax);
+    pointsht_status s = check_device(plan, "synthesis");
+    if (s != POINTSHT_OK) return s;
+    pointsht_catalog cat;
+    synthesis_catalog(x, phi, n, cat);
+    Layout lo;
+    make_layout(plan, &cat, 1, 1, prec, lo);
+    const size_t need = up256(lo.total) + up256((size_t)n * esz);
+    if ((s = check_ws(lo, workspace, ws_bytes, need, "synthesis")) != POINTSHT_OK) return s;
+    if (n == 0) return POINTSHT_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    void* ones = ws + up256(lo.total);
+    cudaError_t e = launch_fill_ones(n, prec == POINTSHT_FP64, ones, st);
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "synthesis: %s", cudaGetErrorString(e));
+    cat.w = ones;
+    void* outs[1] = {out};
+    return run_adjoint(plan, &cat, 1, 1, lo, alm, nullptr, outs, ws, 1, st, "synthesis");
 }
 
 // ------------------------------------------------------- mode coupling --

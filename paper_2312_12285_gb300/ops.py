@@ -261,6 +261,36 @@ def bin_backward_raw(grad_b, edges, lmax, stream=None):
     return out
 
 
+def synthesis(plan: Plan, x: torch.Tensor, phi: torch.Tensor, alm_t: torch.Tensor, precision: str = "fp32",
+              out=None, workspace=None, stream=None) -> torch.Tensor:
+    """f(n_i) = sum_{l, |m| <= l} a_lm Y_lm(n_i) of the real field with m >= 0
+    coefficients alm_t (complex128 [M] or float64 [M, 2]), at the points
+    (x, phi) (pointsht_synthesis)."""
+    lib = _lib.load()
+    dt = _dtype(precision)
+    if x.dtype != dt or phi.dtype != dt or not x.is_cuda:
+        raise TypeError(f"x and phi must be {dt} CUDA tensors")
+    x, phi = x.contiguous(), phi.contiguous()
+    a = alm_t
+    if a.is_complex():
+        a = torch.view_as_real(a.contiguous())
+    a = a.contiguous()
+    if a.dtype != torch.float64 or a.numel() != 2 * plan.nmodes:
+        raise ValueError("alm must hold the plan's packed triangle in complex128")
+    n = x.shape[0]
+    need = lib.pointsht_workspace_size_synthesis(plan.handle, n, _lib.PRECISIONS[precision])
+    if need == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_synthesis")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+    if out is None:
+        out = torch.empty(n, dtype=dt, device=x.device)
+    _lib.check(lib.pointsht_synthesis(plan.handle, _ptr(x), _ptr(phi), n, _lib.PRECISIONS[precision], _ptr(a),
+                                      _ptr(out), _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+               "synthesis")
+    return out
+
+
 # ------------------------------------------------------- mode coupling --
 def _f64_dev(t: torch.Tensor, name: str) -> torch.Tensor:
     if t.dtype != torch.float64 or not t.is_cuda:

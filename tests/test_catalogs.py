@@ -47,3 +47,18 @@ def test_golden_spiral_range():
 def test_log_bin_edges():
     e = catalogs.log_bin_edges(1024, 32)
     assert len(e) == 33 and e[-1] == 1025 and np.all(np.diff(e) > 0) and e[0] >= 1
+
+
+def test_golden_spiral_layout():
+    """Sec. 3.1: N points, cos(theta) on [1 - (2k+1)/N]/2 up to the jitter,
+    azimuths advancing by 2 pi / varphi (varphi the golden ratio), seeded."""
+    wl = catalogs.golden_spiral_workload(4096, 64, jitter=1e-6)
+    c = wl.catalogs[0]
+    assert c.n == 4096 and wl.lmax == 64 and wl.nfield == 1
+    k = np.arange(4096)
+    assert np.max(np.abs(c.x - 0.5 * (1 - (2 * k + 1) / 4096))) <= 1e-5
+    step = 2 * np.pi * np.mod(2 / (1 + np.sqrt(5)), 1.0)
+    dphi = np.mod(np.diff(c.phi.astype(np.float64)) - step + np.pi, 2 * np.pi) - np.pi
+    assert np.max(np.abs(dphi)) <= 1e-5
+    assert np.array_equal(c.x, catalogs.golden_spiral_workload(4096, 64).catalogs[0].x)
+    assert np.all(c.w == 1)
