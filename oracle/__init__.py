@@ -57,6 +57,10 @@ def _load():
             lib.oracle_alm.restype = ctypes.c_int
             lib.oracle_adjoint.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.oracle_adjoint.restype = ctypes.c_int
+            lib.oracle_spin_lambda.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_spin_lambda.restype = None
+            lib.oracle_alm_spin2.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
+            lib.oracle_alm_spin2.restype = ctypes.c_int
             lib.oracle_synthesis.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.oracle_synthesis.restype = ctypes.c_int
             lib.oracle_threej000.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -367,3 +371,29 @@ def fkp_norm(W) -> float:
     W = np.asarray(W, np.float64)
     l = np.arange(W.size)
     return 1.0 / (np.sum((2 * l + 1) * W) / FOUR_PI)
+
+
+# -------------------------------------------------- spin-2 (shear) transform --
+def spin_lambda(x: float, lmax: int, m: int, n: int) -> np.ndarray:
+    """lambda^(n)_lm(x) = sqrt((2l+1)/4pi) d^l_{m,n}(theta), l = 0..lmax (zero
+    below max(m, |n|)); _{+2}Y*_lm = lambda^(-2) e^{-i m phi},
+    _{-2}Y*_lm = lambda^(+2) e^{-i m phi}."""
+    out = np.zeros(lmax + 1, np.float64)
+    _load().oracle_spin_lambda(float(x), int(lmax), int(m), int(n), _dptr(out))
+    return out
+
+
+def alm_spin2(x, phi, w, g1, g2, lmax: int, nthreads: int = 0):
+    """(E_lm, B_lm), packed triangles (complex128), of the spin-2 field
+    (g1, g2) carried by weighted points: _{+-2}a = sum w (g1 +- i g2) _{+-2}Y*,
+    E = -(_{2}a + _{-2}a)/2, B = i(_{2}a - _{-2}a)/2; zero for l < 2."""
+    lib = _load()
+    x, phi, w, g1, g2 = (_f64(v) for v in (x, phi, w, g1, g2))
+    M = nmodes(lmax)
+    E = np.zeros(2 * M, np.float64)
+    B = np.zeros(2 * M, np.float64)
+    rc = lib.oracle_alm_spin2(x.shape[0], _dptr(x), _dptr(phi), _dptr(w), _dptr(g1), _dptr(g2), int(lmax),
+                              _dptr(E), _dptr(B), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_alm_spin2 failed ({rc})")
+    return E[0::2] + 1j * E[1::2], B[0::2] + 1j * B[1::2]

@@ -579,3 +579,168 @@ int oracle_synthesis(int64_t n, const double* x, const double* phi, int lmax, co
     }
     return status;
 }
+
+/* ------------------------------------------------------------------------
+ * Spin-weighted harmonics for a spin-2 (shear) field.  The paper names the
+ * generalisation (Sec. 4: use _{+-2}Y_lm, computed by recurrence) without
+ * printing it; this is the textbook form through Wigner's small d:
+ *
+ *   _sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta) e^{i m phi},
+ *
+ * (for s = 0 the Y_lm of App. A), so for m >= 0
+ *   _{+2}Y*_lm = lambda^(-2)_lm e^{-i m phi},  _{-2}Y*_lm = lambda^(+2)_lm e^{-i m phi},
+ *   lambda^(n)_lm(theta) = sqrt((2l+1)/4pi) d^l_{m,n}(theta).
+ * Seed at l0 = max(m, |n|) from the top row of d,
+ *   d^l_{l,k}(b) = (-1)^(l-k) sqrt((2l)! / ((l+k)! (l-k)!)) cos^(l+k)(b/2) sin^(l-k)(b/2),
+ * with d^l_{m,n} = (-1)^(m-n) d^l_{n,m} = d^l_{-n,-m}; then the three-term
+ * recurrence of d in l at fixed (m, n), written for lambda:
+ *   lambda_{l+1} = (A_l x + B_l) lambda_l - C_l lambda_{l-1},
+ *   A_l = sqrt((2l+3)(2l+1)) (l+1) / R_{l+1},
+ *   B_l = -sqrt((2l+3)(2l+1)) m n / (l R_{l+1}),
+ *   C_l = sqrt((2l+3)/(2l-1)) (l+1) R_l / (l R_{l+1}),
+ *   R_l = sqrt((l^2 - m^2)(l^2 - n^2)).
+ * Values are carried as mantissa and binary exponent like Pbar above (the
+ * seed ~ cos^p(theta/2) sin^q(theta/2) leaves the FP64 range at high m).
+ * The seed's logarithm is taken in long double (lgammal, log2l).
+ *
+ *   _{+-2}a_lm = sum_i w_i (g1 +- i g2)_i _{+-2}Y*_lm(n_i),
+ *   E_lm = -(_{2}a_lm + _{-2}a_lm) / 2,   B_lm = i (_{2}a_lm - _{-2}a_lm) / 2,
+ * the usual E/B split of a spin-2 field (g1, g2) (as for Q, U).
+ * ---------------------------------------------------------------------- */
+static void spin_seed(double x, int m, int n, double* v, int* e, int* l0_out) {
+    const int an = n < 0 ? -n : n;
+    const int l0 = m > an ? m : an;
+    int k, sgn = 1;
+    if (m >= an) {
+        k = n;                        /* d^m_{m,n}: top row */
+    } else if (n > 0) {
+        k = m;                        /* d^n_{m,n} = (-1)^(m-n) d^n_{n,m} */
+        if ((n - m) & 1) sgn = -sgn;
+    } else {
+        k = -m;                       /* d^l0_{m,-l0} = d^l0_{l0,-m} */
+    }
+    if ((l0 - k) & 1) sgn = -sgn;
+    const int pc = l0 + k, ps = l0 - k;
+    const double c2 = 0.5 * (1.0 + x), s2 = 0.5 * (1.0 - x); /* cos^2, sin^2 of theta/2 */
+    *l0_out = l0;
+    if ((pc > 0 && !(c2 > 0.0)) || (ps > 0 && !(s2 > 0.0))) {
+        *v = 0.0;
+        *e = 0;
+        return;
+    }
+    long double lg = 0.5L * log2l((2.0L * l0 + 1.0L) / (4.0L * (long double)ORACLE_PI)) +
+                     0.5L * (lgammal(2.0L * l0 + 1.0L) - lgammal((long double)(l0 + k) + 1.0L) -
+                             lgammal((long double)(l0 - k) + 1.0L)) / logl(2.0L);
+    if (pc > 0) lg += 0.5L * pc * log2l((long double)c2);
+    if (ps > 0) lg += 0.5L * ps * log2l((long double)s2);
+    const long double fl = floorl(lg);
+    *v = sgn * (double)exp2l(lg - fl);
+    *e = (int)fl;
+}
+
+/* lambda^(n)_lm(x) for l = 0..lmax as mantissa/exponent (zero below l0). */
+static void spin_column_scaled(double x, int lmax, int m, int n, double* mant, int* expo) {
+    for (int l = 0; l <= lmax; ++l) {
+        mant[l] = 0.0;
+        expo[l] = 0;
+    }
+    double v;
+    int e, l0;
+    spin_seed(x, m, n, &v, &e, &l0);
+    if (l0 > lmax) return;
+    mant[l0] = v;
+    expo[l0] = e;
+    double pm1 = v, pm2 = 0.0;
+    const double mm = (double)m * m, nn = (double)n * n;
+    for (int l = l0; l < lmax; ++l) {
+        const double dl = (double)l;
+        const double r1 = sqrt(((dl + 1) * (dl + 1) - mm) * ((dl + 1) * (dl + 1) - nn));
+        const double q = sqrt((2 * dl + 3) * (2 * dl + 1));
+        const double A = q * (dl + 1) / r1;
+        const double B = (m == 0 || n == 0) ? 0.0 : -q * (double)m * (double)n / (dl * r1);
+        const double C = (l == l0) ? 0.0
+                                   : sqrt((2 * dl + 3) / (2 * dl - 1)) * (dl + 1) *
+                                         sqrt((dl * dl - mm) * (dl * dl - nn)) / (dl * r1);
+        double p = (A * x + B) * pm1 - C * pm2;
+        pm2 = pm1;
+        pm1 = p;
+        if (e < 0 && fabs(p) > 0x1p256) {
+            pm1 *= 0x1p-256;
+            pm2 *= 0x1p-256;
+            e += ORACLE_SCALE_BITS;
+        }
+        mant[l + 1] = pm1;
+        expo[l + 1] = e;
+    }
+}
+
+void oracle_spin_lambda(double x, int lmax, int m, int n, double* out) {
+    double* mant = (double*)malloc(sizeof(double) * ((size_t)lmax + 1));
+    int* expo = (int*)malloc(sizeof(int) * ((size_t)lmax + 1));
+    spin_column_scaled(x, lmax, m, n, mant, expo);
+    for (int l = 0; l <= lmax; ++l) out[l] = ldexp(mant[l], expo[l]);
+    free(mant);
+    free(expo);
+}
+
+/* E_lm, B_lm (packed m-major triangle, interleaved re/im) of the spin-2
+ * field (g1, g2) carried by weighted points.  One order m per task, points
+ * summed in order with Neumaier accumulators: independent of threads. */
+int oracle_alm_spin2(int64_t np, const double* x, const double* phi, const double* w, const double* g1,
+                     const double* g2, int lmax, double* E, double* B, int nthreads) {
+    if (np < 0 || lmax < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int status = 0;
+#pragma omp parallel
+    {
+        const size_t L1 = (size_t)lmax + 1;
+        double* mp = (double*)malloc(sizeof(double) * L1);
+        double* mq = (double*)malloc(sizeof(double) * L1);
+        int* ep = (int*)malloc(sizeof(int) * L1);
+        int* eq = (int*)malloc(sizeof(int) * L1);
+        nsum* acc = (nsum*)malloc(sizeof(nsum) * 4 * L1);
+        if (!mp || !mq || !ep || !eq || !acc) {
+#pragma omp critical
+            status = -2;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int m = 0; m <= lmax; ++m) {
+                memset(acc, 0, sizeof(nsum) * 4 * L1);
+                for (int64_t i = 0; i < np; ++i) {
+                    spin_column_scaled(x[i], lmax, m, -2, mp, ep); /* _{+2}Y* */
+                    spin_column_scaled(x[i], lmax, m, +2, mq, eq); /* _{-2}Y* */
+                    const double c = cos((double)m * phi[i]), s = -sin((double)m * phi[i]); /* e^{-i m phi} */
+                    const double pr = w[i] * (g1[i] * c - g2[i] * s), pi_ = w[i] * (g1[i] * s + g2[i] * c);
+                    const double qr = w[i] * (g1[i] * c + g2[i] * s), qi = w[i] * (g1[i] * s * 1.0 - g2[i] * c);
+                    for (int l = m > 2 ? m : 2; l <= lmax; ++l) {
+                        const double lp = ldexp(mp[l], ep[l]), lq = ldexp(mq[l], eq[l]);
+                        nsum_add(&acc[4 * l + 0], pr * lp);
+                        nsum_add(&acc[4 * l + 1], pi_ * lp);
+                        nsum_add(&acc[4 * l + 2], qr * lq);
+                        nsum_add(&acc[4 * l + 3], qi * lq);
+                    }
+                }
+                const int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+                for (int l = m; l <= lmax; ++l) {
+                    double ar = 0, ai = 0, br = 0, bi = 0;
+                    if (l >= 2) {
+                        ar = nsum_val(&acc[4 * l]);
+                        ai = nsum_val(&acc[4 * l + 1]);
+                        br = nsum_val(&acc[4 * l + 2]);
+                        bi = nsum_val(&acc[4 * l + 3]);
+                    }
+                    E[2 * (base + l)] = -0.5 * (ar + br);
+                    E[2 * (base + l) + 1] = -0.5 * (ai + bi);
+                    B[2 * (base + l)] = -0.5 * (ai - bi);
+                    B[2 * (base + l) + 1] = 0.5 * (ar - br);
+                }
+            }
+        }
+        free(mp); free(mq); free(ep); free(eq); free(acc);
+    }
+    return status;
+}
