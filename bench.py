@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-coupling", action="store_true", help="skip the mode-coupling matrix measurement")
+    ap.add_argument("--no-spin2", action="store_true", help="skip the spin-2 (shear) transform measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
@@ -422,6 +423,9 @@ def ours(args):
     coupling = None
     if rank == 0 and world == 1 and not args.no_coupling and prec == "fp32" and coef is None:
         coupling = coupling_measure(plan, wl, dev, L)
+    spin2 = None
+    if rank == 0 and world == 1 and not args.no_spin2 and prec == "fp32" and coef is None:
+        spin2 = spin2_measure(plan, wl, dev, L, peak, peak_src)
     ladder = None
     if rank == 0 and world == 1 and not args.no_ladder and prec == "fp32" and wl.nfield == 1:
         ladder = precision_ladder(wl, plan, dev, value, accuracy["cl_err_vs_fp64_oracle"] if accuracy else None,
@@ -460,6 +464,7 @@ def ours(args):
             "precision_ladder": ladder,
             "adjoint": adjoint,
             "coupling": coupling,
+            "spin2": spin2,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -516,6 +521,45 @@ def coupling_measure(plan, wl, dev, L):
                          "kernel": "cp_coupling_kernel (FP64: one multiply + one FMA per term)",
                          "peak_source": "nominal FP64 1.25 TFLOP/s"},
             "what": "M_ll' (Eq. chat) from the randoms' window spectrum, lmax = lmax_w = workload lmax"}
+
+
+def spin2_measure(plan, wl, dev, L, peak, peak_src):
+    """The spin-2 row: E_lm, B_lm of a synthetic shear field (a smooth
+    random-wave pattern plus shape noise, seeded) carried by the workload's
+    galaxies, lmax = workload lmax, timed with CUDA events (one warm-up, one
+    timed call).  Algorithmic flops per point x mode, both spins: recurrence
+    2 x (t = A x + B: 2, C p: 1, FMA: 2) = 10, accumulation 2 x 2 FMA = 8."""
+    import numpy as np
+    import torch
+
+    from paper_2312_12285_gb300 import ops
+    gal = [c for c in wl.catalogs if c.name == "galaxies"]
+    if not gal:
+        return None
+    g = gal[0]
+    rng = np.random.default_rng(31)
+    th = np.arccos(g.x.astype(np.float64))
+    g1 = (0.05 * np.cos(7 * th + 3 * g.phi) + 0.2 * rng.standard_normal(g.n)).astype(np.float32)
+    g2 = (0.05 * np.sin(5 * th - 2 * g.phi) + 0.2 * rng.standard_normal(g.n)).astype(np.float32)
+    cat = ops.ShearCat(*(torch.from_numpy(a).to(dev) for a in (g.x, g.phi, g.w, g1, g2)), 0, 1.0)
+    E, B = ops.alm_spin2(plan, [cat], 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ops.alm_spin2(plan, [cat], 1)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1)
+    nm = (L + 1) * (L + 2) // 2
+    pm = g.n * nm / (ms / 1e3)
+    ach = 18.0 * pm / 1e12
+    return {"value": pm, "unit": UNIT + " (E and B)", "ms": ms, "points": g.n, "lmax": L,
+            "finite": bool(torch.isfinite(E).all() and torch.isfinite(B).all()),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "kernel": "s2_analysis_kernel (one f32x2 recurrence per point for both spins, "
+                                   "18 flops per point x mode)", "peak_source": peak_src},
+            "what": "E_lm, B_lm of a synthetic shear field on the workload's galaxies (Sec. 4 spin-2 variant)"}
 
 
 def adjoint_measure(plan, cats, nfield, prec, out, ws, edges, L, peak, peak_src):

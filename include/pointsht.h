@@ -78,6 +78,21 @@ typedef struct {
     double coeff;     /* coefficient of this catalog in its field */
 } pointsht_catalog;
 
+/* One catalog of a spin-2 (shear) field: positions, weights and the two
+ * components (g1, g2) of the spin-2 quantity at each point (pointsht_alm_spin2).
+ * FP32 device arrays of n values; coeff multiplies w. */
+typedef struct {
+    const void* x;    /* cos(theta) */
+    const void* phi;  /* azimuth (radians) */
+    const void* w;    /* weight */
+    const void* g1;   /* first component (as Q) */
+    const void* g2;   /* second component (as U) */
+    int64_t n;
+    int32_t field;
+    int32_t pad_;     /* set to 0 */
+    double coeff;
+} pointsht_shear_catalog;
+
 /* Opaque plan: recurrence tables for one lmax on one device.  Creating it
  * allocates and fills device tables (this is the only allocating call). */
 typedef struct pointsht_plan_s* pointsht_plan;
@@ -287,6 +302,31 @@ size_t pointsht_workspace_size_synthesis(pointsht_plan plan, int64_t n, pointsht
 pointsht_status pointsht_synthesis(pointsht_plan plan, const void* x, const void* phi, int64_t n,
                                    pointsht_precision prec, const double* alm, void* out, void* workspace,
                                    size_t ws_bytes, void* stream);
+
+/* Spin-2 (shear) transform of weighted point catalogs: the generalisation
+ * to fields of non-zero spin that Sec. 4 names (spin-weighted harmonics
+ * _{+-2}Y_lm from a recurrence):
+ *   _{+-2}a_lm = sum_i coeff w_i (g1 +- i g2)_i _{+-2}Y*_lm(n_i),
+ *   E_lm = -(_{2}a_lm + _{-2}a_lm)/2,  B_lm = i (_{2}a_lm - _{-2}a_lm)/2,
+ * with _sY_lm = (-1)^s sqrt((2l+1)/4pi) d^l_{m,-s}(theta) e^{i m phi} (Wigner's
+ * small d; s = 0 gives the Y_lm of App. A; _{2}Y = sqrt((l-2)!/(l+2)!) eth eth Y
+ * with eth the usual spin-raising operator).  E and B are the coefficients of
+ * real fields (negative m implicit), zero for l < 2.
+ * cats: host array of ncat descriptors (FP32 device arrays); E_out, B_out:
+ * device, nfield*M complex128 each (packed m-major triangle, 16-byte
+ * aligned), overwritten; workspace: >= pointsht_workspace_size_spin2() bytes
+ * (~36 bytes per point + (lmax+1)^2 x 16 bytes + ~M x 32 bytes per chunk of
+ * up to 2^20 points), 256-byte aligned.  FP32 recurrence (one recurrence per
+ * point serves both spins through d^l_{m,2}(theta) =
+ * (-1)^(l+m) d^l_{m,-2}(pi - theta)), FP64 sums over chunks; lmax <= the FP32
+ * path's limit.  |x| > 1 or non-finite inputs: ERANGE at the next
+ * pointsht_plan_check (those points count with zero weight). */
+size_t pointsht_workspace_size_spin2(pointsht_plan plan, const pointsht_shear_catalog* cats, int32_t ncat,
+                                     int32_t nfield);
+
+pointsht_status pointsht_alm_spin2(pointsht_plan plan, const pointsht_shear_catalog* cats, int32_t ncat,
+                                   int32_t nfield, double* E_out, double* B_out, void* workspace, size_t ws_bytes,
+                                   void* stream);
 
 /* ---------------------------------------------------------------------
  * Mode coupling of the masked pseudo-spectrum (Sec. 2.1).

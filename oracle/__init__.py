@@ -61,6 +61,9 @@ def _load():
             lib.oracle_spin_lambda.restype = None
             lib.oracle_alm_spin2.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.oracle_alm_spin2.restype = ctypes.c_int
+            lib.oracle_alm_spin2_cols.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ip,
+                                                  dp, dp, ctypes.c_int]
+            lib.oracle_alm_spin2_cols.restype = ctypes.c_int
             lib.oracle_synthesis.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
             lib.oracle_synthesis.restype = ctypes.c_int
             lib.oracle_threej000.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -397,3 +400,21 @@ def alm_spin2(x, phi, w, g1, g2, lmax: int, nthreads: int = 0):
     if rc != 0:
         raise RuntimeError(f"oracle_alm_spin2 failed ({rc})")
     return E[0::2] + 1j * E[1::2], B[0::2] + 1j * B[1::2]
+
+
+def alm_spin2_cols(x, phi, w, g1, g2, lmax: int, mlist, nthreads: int = 0):
+    """{m: (E column, B column)} over l = 0..lmax (zero below max(m, 2)) for
+    the orders in mlist, summed over a fixed partition of the points."""
+    lib = _load()
+    x, phi, w, g1, g2 = (_f64(v) for v in (x, phi, w, g1, g2))
+    ms = np.ascontiguousarray(np.asarray(mlist, np.int32))
+    E = np.zeros(2 * ms.size * (lmax + 1), np.float64)
+    B = np.zeros_like(E)
+    rc = lib.oracle_alm_spin2_cols(x.shape[0], _dptr(x), _dptr(phi), _dptr(w), _dptr(g1), _dptr(g2), int(lmax),
+                                   int(ms.size), ms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(E), _dptr(B),
+                                   int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_alm_spin2_cols failed ({rc})")
+    E = (E[0::2] + 1j * E[1::2]).reshape(ms.size, lmax + 1)
+    B = (B[0::2] + 1j * B[1::2]).reshape(ms.size, lmax + 1)
+    return {int(m): (E[t], B[t]) for t, m in enumerate(ms)}

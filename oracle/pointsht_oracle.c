@@ -744,3 +744,75 @@ int oracle_alm_spin2(int64_t np, const double* x, const double* phi, const doubl
     }
     return status;
 }
+
+/* The same E/B transform for a list of orders only, summed over a fixed
+ * partition of the points (64 contiguous ranges, Neumaier sums combined in
+ * order): for sampled columns of large catalogs.  E/B out: [nm][lmax+1]
+ * interleaved re/im, zero for l < max(m, 2). */
+int oracle_alm_spin2_cols(int64_t np, const double* x, const double* phi, const double* w, const double* g1,
+                          const double* g2, int lmax, int nm, const int* mlist, double* E, double* B, int nthreads) {
+    if (np < 0 || lmax < 0 || nm < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    const size_t L1 = (size_t)lmax + 1;
+    for (int t = 0; t < nm; ++t) {
+        const int m = mlist[t];
+        if (m < 0 || m > lmax) return -3;
+        nsum* part = (nsum*)calloc((size_t)ORACLE_NBLOCKS * 4 * L1, sizeof(nsum));
+        if (!part) return -2;
+        int status = 0;
+#pragma omp parallel
+        {
+            double* mp = (double*)malloc(sizeof(double) * L1);
+            double* mq = (double*)malloc(sizeof(double) * L1);
+            int* ep = (int*)malloc(sizeof(int) * L1);
+            int* eq = (int*)malloc(sizeof(int) * L1);
+            if (!mp || !mq || !ep || !eq) {
+#pragma omp critical
+                status = -2;
+            } else {
+#pragma omp for schedule(dynamic, 1)
+                for (int blk = 0; blk < ORACLE_NBLOCKS; ++blk) {
+                    const int64_t i0 = np * blk / ORACLE_NBLOCKS, i1 = np * (blk + 1) / ORACLE_NBLOCKS;
+                    nsum* acc = part + (size_t)blk * 4 * L1;
+                    for (int64_t i = i0; i < i1; ++i) {
+                        spin_column_scaled(x[i], lmax, m, -2, mp, ep);
+                        spin_column_scaled(x[i], lmax, m, +2, mq, eq);
+                        const double c = cos((double)m * phi[i]), s = -sin((double)m * phi[i]);
+                        const double pr = w[i] * (g1[i] * c - g2[i] * s), pi_ = w[i] * (g1[i] * s + g2[i] * c);
+                        const double qr = w[i] * (g1[i] * c + g2[i] * s), qi = w[i] * (g1[i] * s - g2[i] * c);
+                        for (int l = m > 2 ? m : 2; l <= lmax; ++l) {
+                            const double lp = ldexp(mp[l], ep[l]), lq = ldexp(mq[l], eq[l]);
+                            nsum_add(&acc[4 * l + 0], pr * lp);
+                            nsum_add(&acc[4 * l + 1], pi_ * lp);
+                            nsum_add(&acc[4 * l + 2], qr * lq);
+                            nsum_add(&acc[4 * l + 3], qi * lq);
+                        }
+                    }
+                }
+            }
+            free(mp); free(mq); free(ep); free(eq);
+        }
+        if (status) {
+            free(part);
+            return status;
+        }
+        for (size_t l = 0; l < L1; ++l) {
+            nsum tot[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int blk = 0; blk < ORACLE_NBLOCKS; ++blk)
+                for (int c = 0; c < 4; ++c) nsum_add(&tot[c], nsum_val(&part[((size_t)blk * 4 * L1) + 4 * l + c]));
+            const double ar = nsum_val(&tot[0]), ai = nsum_val(&tot[1]), br = nsum_val(&tot[2]), bi = nsum_val(&tot[3]);
+            double* e = E + 2 * ((size_t)t * L1 + l);
+            double* b = B + 2 * ((size_t)t * L1 + l);
+            e[0] = -0.5 * (ar + br);
+            e[1] = -0.5 * (ai + bi);
+            b[0] = -0.5 * (ai - bi);
+            b[1] = 0.5 * (ar - br);
+        }
+        free(part);
+    }
+    return 0;
+}

@@ -28,9 +28,16 @@ EXPORTS = (
     "pointsht_workspace_size_columns", "pointsht_alm_columns",
     "pointsht_workspace_size_interp", "pointsht_alm_interp",
     "pointsht_workspace_size_synthesis", "pointsht_synthesis",
+    "pointsht_workspace_size_spin2", "pointsht_alm_spin2",
     "pointsht_workspace_size_coupling", "pointsht_coupling", "pointsht_coupling_binned",
     "pointsht_workspace_size_decouple", "pointsht_decouple", "pointsht_fkp_normalise",
 )
+
+
+class ShearCatalog(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("w", ctypes.c_void_p), ("g1", ctypes.c_void_p),
+                ("g2", ctypes.c_void_p), ("n", ctypes.c_int64), ("field", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("coeff", ctypes.c_double)]
 
 
 class Catalog(ctypes.Structure):
@@ -87,6 +94,8 @@ def load(build_if_missing: bool = True):
             "pointsht_alm_interp": ([vp, cp, i32, i32, i32, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_workspace_size_synthesis": ([vp, i64, ctypes.c_int], sz),
             "pointsht_synthesis": ([vp, vp, vp, i64, ctypes.c_int, dp, vp, vp, sz, vp], ctypes.c_int),
+            "pointsht_workspace_size_spin2": ([vp, ctypes.POINTER(ShearCatalog), i32, i32], sz),
+            "pointsht_alm_spin2": ([vp, ctypes.POINTER(ShearCatalog), i32, i32, dp, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_workspace_size_coupling": ([i32], sz),
             "pointsht_coupling": ([i32, i32, dp, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_coupling_binned": ([i32, dp, vp, i32, dp, dp, vp], ctypes.c_int),

@@ -37,6 +37,9 @@ int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
 int adjoint_sorted_points_per_warp();
 size_t coupling_smem_bytes(int);
+size_t spin2_workspace_bytes(int, const pointsht_shear_catalog*, int, int);
+cudaError_t spin2_run(int, const pointsht_shear_catalog*, int, int, void*, unsigned*, int, double*, double*,
+                      cudaStream_t);
 cudaError_t launch_coupling(int, int, const double*, double*, double*, double*, cudaStream_t);
 cudaError_t launch_coupling_binned(int, const double*, const int*, int, double*, double*, cudaStream_t);
 size_t decouple_workspace_bytes(int);
@@ -1195,6 +1198,58 @@ extern "C" pointsht_status pointsht_synthesis(pointsht_plan plan, const void* x,
     cat.w = ones;
     void* outs[1] = {out};
     return run_adjoint(plan, &cat, 1, 1, lo, alm, nullptr, outs, ws, 1, st, "synthesis");
+}
+
+// ------------------------------------------------------------ spin 2 --
+static pointsht_status check_spin2(pointsht_plan plan, const pointsht_shear_catalog* cats, int32_t ncat,
+                                   int32_t nfield, const char* who) {
+    if (!plan) return fail(POINTSHT_EINVAL, "%s: plan is NULL", who);
+    if (ncat < 0 || ncat > PSHT_MAX_CATS) return fail(POINTSHT_EINVAL, "%s: ncat=%d outside [0, %d]", who, ncat, PSHT_MAX_CATS);
+    if (ncat > 0 && !cats) return fail(POINTSHT_EINVAL, "%s: cats is NULL", who);
+    if (nfield < 1 || nfield > PSHT_MAX_FIELDS)
+        return fail(POINTSHT_EINVAL, "%s: nfield=%d outside [1, %d]", who, nfield, PSHT_MAX_FIELDS);
+    if (plan->lmax > F32Scale::MAX_LMAX)
+        return fail(POINTSHT_EINVAL, "%s: the FP32 path supports lmax <= %d (plan has %d)", who, F32Scale::MAX_LMAX,
+                    plan->lmax);
+    for (int c = 0; c < ncat; ++c) {
+        const pointsht_shear_catalog& k = cats[c];
+        if (k.n < 0) return fail(POINTSHT_EINVAL, "%s: catalog %d has n=%lld < 0", who, c, (long long)k.n);
+        if (k.field < 0 || k.field >= nfield)
+            return fail(POINTSHT_EINVAL, "%s: catalog %d has field %d outside [0, %d)", who, c, k.field, nfield);
+        if (!std::isfinite(k.coeff)) return fail(POINTSHT_EINVAL, "%s: catalog %d has a non-finite coeff", who, c);
+        if (k.n > 0) {
+            if (!k.x || !k.phi || !k.w || !k.g1 || !k.g2)
+                return fail(POINTSHT_EINVAL, "%s: catalog %d has a NULL array", who, c);
+            if (((uintptr_t)k.x | (uintptr_t)k.phi | (uintptr_t)k.w | (uintptr_t)k.g1 | (uintptr_t)k.g2) % 4)
+                return fail(POINTSHT_EINVAL, "%s: catalog %d arrays are not 4-byte aligned", who, c);
+        }
+    }
+    return POINTSHT_OK;
+}
+
+extern "C" size_t pointsht_workspace_size_spin2(pointsht_plan plan, const pointsht_shear_catalog* cats, int32_t ncat,
+                                                int32_t nfield) {
+    if (check_spin2(plan, cats, ncat, nfield, "workspace_size_spin2") != POINTSHT_OK) return 0;
+    return spin2_workspace_bytes(plan->lmax, cats, ncat, nfield);
+}
+
+extern "C" pointsht_status pointsht_alm_spin2(pointsht_plan plan, const pointsht_shear_catalog* cats, int32_t ncat,
+                                              int32_t nfield, double* E_out, double* B_out, void* workspace,
+                                              size_t ws_bytes, void* stream) {
+    pointsht_status s = check_spin2(plan, cats, ncat, nfield, "alm_spin2");
+    if (s != POINTSHT_OK) return s;
+    if (!E_out || !B_out || (((uintptr_t)E_out | (uintptr_t)B_out) % 16))
+        return fail(POINTSHT_EINVAL, "alm_spin2: E_out or B_out NULL or not 16-byte aligned");
+    if ((s = check_device(plan, "alm_spin2")) != POINTSHT_OK) return s;
+    const size_t need = spin2_workspace_bytes(plan->lmax, cats, ncat, nfield);
+    if (need == 0) return fail(POINTSHT_EINVAL, "alm_spin2: too many points for the chunk table");
+    if (!workspace || ((uintptr_t)workspace % 256))
+        return fail(POINTSHT_EINVAL, "alm_spin2: workspace NULL or not 256-byte aligned");
+    if (ws_bytes < need) return fail(POINTSHT_ENOMEM, "alm_spin2: workspace has %zu bytes, %zu needed", ws_bytes, need);
+    cudaError_t e = spin2_run(plan->lmax, cats, ncat, nfield, workspace, plan->err, plan->sm_count, E_out, B_out,
+                              static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_spin2: %s", cudaGetErrorString(e));
+    return POINTSHT_OK;
 }
 
 // ------------------------------------------------------- mode coupling --

@@ -291,6 +291,50 @@ def synthesis(plan: Plan, x: torch.Tensor, phi: torch.Tensor, alm_t: torch.Tenso
     return out
 
 
+# ------------------------------------------------------------- spin 2 --
+class ShearCat:
+    """A catalog of a spin-2 field: float32 CUDA tensors x = cos(theta), phi,
+    w and the two components g1, g2 at each point; its field and coefficient."""
+
+    def __init__(self, x, phi, w, g1, g2, field: int = 0, coeff: float = 1.0):
+        self.x, self.phi, self.w, self.g1, self.g2 = x, phi, w, g1, g2
+        self.field, self.coeff = int(field), float(coeff)
+
+
+def _shear_entries(cats):
+    arr = (_lib.ShearCatalog * max(1, len(cats)))()
+    keep = []
+    for i, c in enumerate(cats):
+        ts = [t.contiguous() for t in (c.x, c.phi, c.w, c.g1, c.g2)]
+        for t in ts:
+            if t.dtype != torch.float32 or not t.is_cuda:
+                raise TypeError("shear catalog arrays must be float32 CUDA tensors")
+        n = ts[0].shape[0]
+        if any(t.shape[0] != n for t in ts):
+            raise ValueError("shear catalog arrays differ in length")
+        keep.extend(ts)
+        arr[i] = _lib.ShearCatalog(*(t.data_ptr() if n else None for t in ts), n, c.field, 0, c.coeff)
+    return arr, keep
+
+
+def alm_spin2(plan: Plan, cats, nfield: int = 1, workspace=None, stream=None):
+    """(E, B): complex128 [nfield, M] of the spin-2 field (g1, g2) carried by
+    the catalogs (pointsht_alm_spin2)."""
+    lib = _lib.load()
+    arr, keep = _shear_entries(cats)
+    need = lib.pointsht_workspace_size_spin2(plan.handle, arr, len(cats), nfield)
+    if need == 0:
+        _lib.check(_lib.EINVAL, "workspace_size_spin2")
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=plan.device)
+    E = torch.empty((nfield, plan.nmodes), dtype=torch.complex128, device=plan.device)
+    B = torch.empty_like(E)
+    _lib.check(lib.pointsht_alm_spin2(plan.handle, arr, len(cats), nfield, _ptr(E), _ptr(B), _ptr(workspace),
+                                      workspace.numel(), _stream_ptr(stream)), "alm_spin2")
+    del keep
+    return E, B
+
+
 # ------------------------------------------------------- mode coupling --
 def _f64_dev(t: torch.Tensor, name: str) -> torch.Tensor:
     if t.dtype != torch.float64 or not t.is_cuda:

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     text = open(os.path.join(ROOT, "include", "pointsht.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pointsht_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(pointsht_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -162,3 +162,16 @@ def test_high_m_near_pole_stays_finite_and_matches_log_form():
         assert abs(abs(got) / np.exp(logv) - 1.0) <= 1e-10
     mid = oracle.spin_lambda(0.3, L, 1500, -2)
     assert np.all(np.isfinite(mid)) and np.max(np.abs(mid)) > 0.1
+
+
+def test_column_form_matches_full_transform():
+    rng = np.random.default_rng(11)
+    n, L = 500, 24
+    x, phi = rng.uniform(-1, 1, n), rng.uniform(0, 2 * np.pi, n)
+    w, g1, g2 = rng.uniform(0.5, 1.5, n), rng.standard_normal(n), rng.standard_normal(n)
+    E, B = oracle.alm_spin2(x, phi, w, g1, g2, L)
+    cols = oracle.alm_spin2_cols(x, phi, w, g1, g2, L, [0, 1, 5, 24])
+    for m, (ec, bc) in cols.items():
+        sl = slice(oracle.index(m, m, L), oracle.index(L, m, L) + 1)
+        assert np.allclose(ec[m:], E[sl], rtol=1e-12, atol=1e-12)
+        assert np.allclose(bc[m:], B[sl], rtol=1e-12, atol=1e-12)
