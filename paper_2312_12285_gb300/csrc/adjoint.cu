@@ -11,6 +11,11 @@
 // floating-point range (exponent block E < 0) are dropped by clearing that
 // point's accumulators when E reaches 0, and at the end of a column if it
 // never does.  Sums over m are carried in FP64 per point.
+//
+// Two kernels: adjoint_kernel (FP64, catalog order, K = 2 points per lane)
+// and adjoint_sorted_kernel (FP32, over the analysis's |x|-sorted prepared
+// points, 8 per lane as f32x2 pairs).  Point-evaluation synthesis is the same
+// computation with unit weights (see build_gtab_kernel).
 #include "common.cuh"
 
 #include <math_constants.h>
@@ -19,43 +24,10 @@
 
 namespace psht {
 
-// Seed, phase and coefficient loads for the adjoint, from per-point values
-// held in registers (the analysis reads them from its shared-memory tile).
+// Seed, phase and coefficient loads for the FP64 adjoint, from per-point
+// values held in registers (the analysis reads them from its shared-memory
+// tile).
 namespace adj {
-
-struct F32 {
-    using real = float;
-    using real2 = float2;
-    __device__ static __forceinline__ void seed(int m, double ls, float lch, float lcl, float& mant, int& E) {
-        const float lh = (float)ls;
-        seed_f32(m, lh, (float)(ls - (double)lh), lch, lcl, mant, E);
-    }
-    __device__ static __forceinline__ void phase(int m, uint64_t turn, float& cs, float& sn) {
-        phase_f32(m, (uint32_t)(turn >> 32), (uint32_t)turn, cs, sn);
-    }
-    __device__ static __forceinline__ float down(float v) { return v * 0x1p-64f; }
-    __device__ static __forceinline__ float thresh() { return 0x1p-61f; }
-    __device__ static __forceinline__ void load16(const float2* g, float2 (&v)[16]) {
-        const float4* g4 = reinterpret_cast<const float4*>(g);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float4 t = __ldg(g4 + c);
-            v[2 * c] = make_float2(t.x, t.y);
-            v[2 * c + 1] = make_float2(t.z, t.w);
-        }
-    }
-    __device__ static __forceinline__ void load16a(const float* a, float (&v)[16]) {
-        const float4* a4 = reinterpret_cast<const float4*>(a);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float4 t = __ldg(a4 + c);
-            v[4 * c] = t.x;
-            v[4 * c + 1] = t.y;
-            v[4 * c + 2] = t.z;
-            v[4 * c + 3] = t.w;
-        }
-    }
-};
 
 struct F64 {
     using real = double;
@@ -477,23 +449,20 @@ __global__ void build_gtab_kernel(int L, const double2* __restrict__ galm, const
 cudaError_t launch_build_gtab(int is_f64, int L, int nfield, const double* galm, const double* gamma,
                               const int64_t* colstart, int64_t gstride, int synth, void* gtab, cudaStream_t st) {
     dim3 grid(4, L + 1, nfield);
-    if (is_f64)
-        build_gtab_kernel<double2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
-                                                         gstride, synth, static_cast<double2*>(gtab));
-    else
-        build_gtab_kernel<float2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
-                                                        gstride, synth, static_cast<float2*>(gtab));
+    if (!is_f64) return cudaErrorInvalidValue;  // FP32 uses build_gtab4_kernel (sorted adjoint)
+    build_gtab_kernel<double2><<<grid, 256, 0, st>>>(L, reinterpret_cast<const double2*>(galm), gamma, colstart,
+                                                     gstride, synth, static_cast<double2*>(gtab));
     return cudaGetLastError();
 }
 
-int adjoint_points_per_warp(int is_f64) { return is_f64 ? 32 * 2 : 32 * 4; }
+int adjoint_points_per_warp(int is_f64) { return is_f64 ? 32 * 2 : 0; }
 
 cudaError_t launch_adjoint(int is_f64, const AdjointParams& ap, cudaStream_t st) {
     const int64_t nwarps = ap.warp0[ap.ncat];
     if (nwarps == 0) return cudaSuccess;
     const int64_t nblocks = (nwarps + 3) / 4;
-    if (is_f64) adjoint_kernel<adj::F64, double, 2><<<(unsigned)nblocks, 128, 0, st>>>(ap);
-    else adjoint_kernel<adj::F32, float, 4><<<(unsigned)nblocks, 128, 0, st>>>(ap);
+    if (!is_f64) return cudaErrorInvalidValue;  // FP32 runs adjoint_sorted_kernel
+    adjoint_kernel<adj::F64, double, 2><<<(unsigned)nblocks, 128, 0, st>>>(ap);
     return cudaGetLastError();
 }
 
