@@ -528,7 +528,7 @@ def spin2_measure(plan, wl, dev, L, peak, peak_src):
     random-wave pattern plus shape noise, seeded) carried by the workload's
     galaxies, lmax = workload lmax, timed with CUDA events (one warm-up, one
     timed call).  Algorithmic flops per point x mode, both spins: recurrence
-    2 x (t = A x + B: 2, C p: 1, FMA: 2) = 10, accumulation 2 x 2 FMA = 8."""
+    2 x (t = A' x + B': 2, tau = t p1 + p2: 2) = 8, accumulation 2 x 2 FMA = 8."""
     import numpy as np
     import torch
 
@@ -553,12 +553,12 @@ def spin2_measure(plan, wl, dev, L, peak, peak_src):
     ms = e0.elapsed_time(e1)
     nm = (L + 1) * (L + 2) // 2
     pm = g.n * nm / (ms / 1e3)
-    ach = 18.0 * pm / 1e12
+    ach = 16.0 * pm / 1e12
     return {"value": pm, "unit": UNIT + " (E and B)", "ms": ms, "points": g.n, "lmax": L,
             "finite": bool(torch.isfinite(E).all() and torch.isfinite(B).all()),
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                          "kernel": "s2_analysis_kernel (one f32x2 recurrence per point for both spins, "
-                                   "18 flops per point x mode)", "peak_source": peak_src},
+                                   "16 flops per point x mode)", "peak_source": peak_src},
             "what": "E_lm, B_lm of a synthetic shear field on the workload's galaxies (Sec. 4 spin-2 variant)"}
 
 

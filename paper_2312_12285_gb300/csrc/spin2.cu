@@ -17,9 +17,15 @@
 //   seed = (-1)^m sqrt((2 l0 + 1)/4pi) sqrt((2 l0)! / ((l0+k)! (l0-k)!))
 //          cos^|m-2|(theta/2) sin^(m+2)(theta/2),  k = -2 (m >= 2) or -m,
 // taken in log2 (FP32 hi + lo) with the same exponent blocks as the scalar
-// path.  Per point and step: t = A (x, -x) + B, lambda = t * p1 - C * p2, and
-// two accumulations (re of both spins, im of both spins): five packed f32x2
-// instructions.
+// path.  As for the scalar path, the recurrence runs in a rescaled,
+// sign-folded variable tau_l = lambda_l / (g_l eps_l) with g_{l+1} = C_l g_{l-1}
+// (g = 1 at l0, l0 + 1) and eps_{l+1} = -eps_{l-1}, so that
+//   tau_{l+1} = (A'_l x + B'_l) tau_l + tau_{l-1},
+//   A'_l, B'_l = (A_l, B_l) g_l eps_l / (g_{l+1} eps_{l+1}),
+// and g_l eps_l multiplies the FP32 row sums when they are added into the
+// FP64 slots.  Per point and step: t = A' (x, -x) + B', tau = t p1 + p2, and
+// two accumulations (re of both spins, im of both spins): four packed f32x2
+// FMAs.
 //
 // Work: a unit is (order m, chunk of points of one field); a CTA of 4 warps
 // takes units from a global counter (largest l-range first).  Each warp runs
@@ -79,7 +85,8 @@ struct S2Params {
     int32_t lmax, nchunk;
     int64_t ntot, nmodes, cstride;
     const float* pts;
-    const float4* coef;   // [lmax+1][cstride] (A, B, -C, 0) per step
+    const float2* coef;   // [lmax+1][cstride] (A', B') per step
+    const double* scale;  // [lmax+1][cstride] g_l eps_l per step
     const float4* seedc;  // [lmax+1] (log2 c hi, lo, |m-2|, m+2)
     double4* slots;       // [nchunk][nmodes] (re+, im+, re-, im-)
     int* counter;
@@ -163,40 +170,51 @@ __global__ void s2_prep_kernel(const __grid_constant__ S2PrepParams p) {
     }
 }
 
-// Recurrence coefficients and seed constants, FP64 then rounded.  Step q of
-// order m produces lambda_{l0+q}: q = 0 is the seed (A = B = 0, -C = 1 with
-// p1 = 0, p2 = seed), step q >= 1 applies the coefficients of l = l0 + q - 1.
-// Entries past the column are zero.
-__global__ void s2_coef_kernel(int L, int64_t cstride, float4* __restrict__ coef, float4* __restrict__ seedc) {
-    const int m = blockIdx.y;
+// Recurrence coefficients, row scales and seed constants, FP64 (the
+// coefficients then rounded once).  Step q of order m produces tau_{l0+q}:
+// q = 0 is the seed (p1 = 0, p2 = seed: tau = t 0 + p2), step q >= 1 applies
+// the coefficients of l = l0 + q - 1.  One thread per order (g is a running
+// product along l); entries past the column are zero.
+__global__ void s2_coef_kernel(int L, int64_t cstride, float2* __restrict__ coef, double* __restrict__ scale,
+                               float4* __restrict__ seedc) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > L) return;
     const int l0 = max(m, 2);
     const int len = L - l0 + 1;
     const double mm = (double)m * m, nn = 4.0;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cstride;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2* cm = coef + (int64_t)m * cstride;
+    double* sm = scale + (int64_t)m * cstride;
+    double g2 = 1.0, g1 = 1.0;  // g eps of l - 1 and l (signed)
+    for (int64_t q = 0; q < cstride; ++q) {
+        float2 v = make_float2(0.f, 0.f);
+        double sc = 0.0;
         if (q == 0 && len > 0) {
-            v.z = 1.f;
+            sc = 1.0;
         } else if (q < len) {
             const double l = (double)(l0 + q - 1);
             const double r1 = sqrt(((l + 1) * (l + 1) - mm) * ((l + 1) * (l + 1) - nn));
             const double qq = sqrt((2 * l + 3) * (2 * l + 1));
             const double A = qq * (l + 1) / r1;
             const double B = 2.0 * qq * (double)m / (l * r1);  // -qq m n / (l R), n = -2
-            const double C = q == 1 ? 0.0 : sqrt((2 * l + 3) / (2 * l - 1)) * (l + 1) * sqrt((l * l - mm) * (l * l - nn)) /
-                                                 (l * r1);
-            v = make_float4((float)A, (float)B, (float)(-C), 0.f);
+            // g eps of l + 1: 1 at l0 + 1, else -C_l (g eps of l - 1)
+            const double gn = q == 1 ? 1.0
+                                     : -(sqrt((2 * l + 3) / (2 * l - 1)) * (l + 1) * sqrt((l * l - mm) * (l * l - nn)) /
+                                         (l * r1)) * g2;
+            const double f = g1 / gn;
+            v = make_float2((float)(A * f), (float)(B * f));
+            sc = gn;
+            g2 = g1;
+            g1 = gn;
         }
-        coef[(int64_t)m * cstride + q] = v;
+        cm[q] = v;
+        sm[q] = sc;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const int k = m >= 2 ? -2 : -m;
-        const double lg = 0.5 * log2((2.0 * l0 + 1.0) / (4.0 * CUDART_PI)) +
-                          0.5 * (lgamma(2.0 * l0 + 1.0) - lgamma((double)(l0 + k) + 1.0) -
-                                 lgamma((double)(l0 - k) + 1.0)) / CUDART_LN2;
-        const float hi = (float)lg;
-        seedc[m] = make_float4(hi, (float)(lg - (double)hi), (float)(l0 + k), (float)(l0 - k));
-    }
+    const int k = m >= 2 ? -2 : -m;
+    const double lg = 0.5 * log2((2.0 * l0 + 1.0) / (4.0 * CUDART_PI)) +
+                      0.5 * (lgamma(2.0 * l0 + 1.0) - lgamma((double)(l0 + k) + 1.0) - lgamma((double)(l0 - k) + 1.0)) /
+                          CUDART_LN2;
+    const float hi = (float)lg;
+    seedc[m] = make_float4(hi, (float)(lg - (double)hi), (float)(l0 + k), (float)(l0 - k));
 }
 
 // log2 of the seed magnitude c + pc a + ps b (a, b = log2 cos, log2 sin of the
@@ -268,7 +286,8 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
         for (int q = threadIdx.x; q < nblk * 16; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         const float4 sc = p.seedc[m];
-        const float4* coef = p.coef + (int64_t)m * p.cstride;
+        const float2* coef = p.coef + (int64_t)m * p.cstride;
+        const double* rowscale = p.scale + (int64_t)m * p.cstride;
         double4* slot = p.slots + (int64_t)ci * p.nmodes + tri_base(m, L) + l0;
         const int nround = ch.n / S2_ROUND;
         bool first_flush = true;
@@ -298,17 +317,18 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
             bool any_neg = __any_sync(0xffffffffu, lane_neg);
             bool all_dead = __all_sync(0xffffffffu, lane_dead);
             for (int bk = 0; bk < nblk; ++bk) {
-                const float4* cb = coef + bk * 16;
+                const float4* cb = reinterpret_cast<const float4*>(coef + bk * 16);  // two steps per float4
                 const bool skip = all_dead;
                 if (skip) {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c = __ldg(cb + j);
-                        const float2 A2 = make_float2(c.x, c.x), B2 = make_float2(c.y, c.y), C2 = make_float2(c.z, c.z);
+                        const float4 c2 = __ldg(cb + (j >> 1));
+                        const float a = (j & 1) ? c2.z : c2.x, b = (j & 1) ? c2.w : c2.y;
+                        const float2 A2 = make_float2(a, a), B2 = make_float2(b, b);
 #pragma unroll
                         for (int k = 0; k < S2_K; ++k) {
                             const float2 t = s2_fma2(A2, x2[k], B2);
-                            const float2 lam = s2_fma2(t, p1[k], s2_mul2(C2, p2[k]));
+                            const float2 lam = s2_fma2(t, p1[k], p2[k]);
                             p2[k] = p1[k];
                             p1[k] = lam;
                         }
@@ -316,13 +336,14 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
                 } else {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c = __ldg(cb + j);
-                        const float2 A2 = make_float2(c.x, c.x), B2 = make_float2(c.y, c.y), C2 = make_float2(c.z, c.z);
+                        const float4 c2 = __ldg(cb + (j >> 1));
+                        const float a = (j & 1) ? c2.z : c2.x, b = (j & 1) ? c2.w : c2.y;
+                        const float2 A2 = make_float2(a, a), B2 = make_float2(b, b);
                         float2 ra = make_float2(0.f, 0.f), ia = ra, rb = ra, ib = ra;
 #pragma unroll
                         for (int k = 0; k < S2_K; ++k) {
                             const float2 t = s2_fma2(A2, x2[k], B2);
-                            const float2 lam = s2_fma2(t, p1[k], s2_mul2(C2, p2[k]));
+                            const float2 lam = s2_fma2(t, p1[k], p2[k]);
                             p2[k] = p1[k];
                             p1[k] = lam;
                             if (k & 1) {
@@ -410,11 +431,12 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
             if ((r + 1) % S2_FLUSH == 0 || r + 1 == nround) {
                 for (int q = threadIdx.x; q < len; q += blockDim.x) {
                     const float4 a = acc[q];
+                    const double g = rowscale[q];
                     double4 s = first_flush ? make_double4(0.0, 0.0, 0.0, 0.0) : slot[q];
-                    s.x += (double)a.x;
-                    s.y += (double)a.y;
-                    s.z += (double)a.z;
-                    s.w += (double)a.w;
+                    s.x += g * (double)a.x;
+                    s.y += g * (double)a.y;
+                    s.z += g * (double)a.z;
+                    s.w += g * (double)a.w;
                     slot[q] = s;
                     acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -461,7 +483,7 @@ struct S2Layout {
     int nchunk = 0;
     S2Chunk chunk[S2_MAXCHUNK];
     int32_t chunk0[PSHT_MAX_FIELDS + 1] = {};
-    size_t pts_off = 0, coef_off = 0, seed_off = 0, slots_off = 0, counter_off = 0, total = 0;
+    size_t pts_off = 0, coef_off = 0, scale_off = 0, seed_off = 0, slots_off = 0, counter_off = 0, total = 0;
 };
 
 static size_t s2_up256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -508,7 +530,9 @@ static bool spin2_layout(int L, const S2Catalog* cats, int ncat, int nfield, S2L
     lo.pts_off = b;
     b += s2_up256((size_t)ntot * S2_NARR * 4);
     lo.coef_off = b;
-    b += s2_up256((size_t)(L + 1) * lo.cstride * 16);
+    b += s2_up256((size_t)(L + 1) * lo.cstride * 8);
+    lo.scale_off = b;
+    b += s2_up256((size_t)(L + 1) * lo.cstride * 8);
     lo.seed_off = b;
     b += s2_up256((size_t)(L + 1) * 16);
     lo.slots_off = b;
@@ -551,9 +575,10 @@ static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfie
         s2_prep_kernel<<<dim3((unsigned)bx, ncat + nfield), 256, 0, st>>>(pp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    float4* coef = reinterpret_cast<float4*>(ws + lo.coef_off);
+    float2* coef = reinterpret_cast<float2*>(ws + lo.coef_off);
+    double* scale = reinterpret_cast<double*>(ws + lo.scale_off);
     float4* seedc = reinterpret_cast<float4*>(ws + lo.seed_off);
-    s2_coef_kernel<<<dim3(4, L + 1), 256, 0, st>>>(L, lo.cstride, coef, seedc);
+    s2_coef_kernel<<<(L + 1 + 63) / 64, 64, 0, st>>>(L, lo.cstride, coef, scale, seedc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     double4* slots = reinterpret_cast<double4*>(ws + lo.slots_off);
     if (lo.nchunk > 0 && L >= 2) {
@@ -567,6 +592,7 @@ static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfie
         kp->cstride = lo.cstride;
         kp->pts = reinterpret_cast<const float*>(ws + lo.pts_off);
         kp->coef = coef;
+        kp->scale = scale;
         kp->seedc = seedc;
         kp->slots = slots;
         kp->counter = reinterpret_cast<int*>(ws + lo.counter_off);
