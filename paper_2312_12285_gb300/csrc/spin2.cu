@@ -85,7 +85,7 @@ struct S2Params {
     int32_t lmax, nchunk;
     int64_t ntot, nmodes, cstride;
     const float* pts;
-    const float2* coef;   // [lmax+1][cstride] (A', B') per step
+    const float4* coef;   // [lmax+1][cstride] (A', A', B', B') per step (f32x2 operand pairs)
     const double* scale;  // [lmax+1][cstride] g_l eps_l per step
     const float4* seedc;  // [lmax+1] (log2 c hi, lo, |m-2|, m+2)
     double4* slots;       // [nchunk][nmodes] (re+, im+, re-, im-)
@@ -175,18 +175,18 @@ __global__ void s2_prep_kernel(const __grid_constant__ S2PrepParams p) {
 // q = 0 is the seed (p1 = 0, p2 = seed: tau = t 0 + p2), step q >= 1 applies
 // the coefficients of l = l0 + q - 1.  One thread per order (g is a running
 // product along l); entries past the column are zero.
-__global__ void s2_coef_kernel(int L, int64_t cstride, float2* __restrict__ coef, double* __restrict__ scale,
+__global__ void s2_coef_kernel(int L, int64_t cstride, float4* __restrict__ coef, double* __restrict__ scale,
                                float4* __restrict__ seedc) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m > L) return;
     const int l0 = max(m, 2);
     const int len = L - l0 + 1;
     const double mm = (double)m * m, nn = 4.0;
-    float2* cm = coef + (int64_t)m * cstride;
+    float4* cm = coef + (int64_t)m * cstride;
     double* sm = scale + (int64_t)m * cstride;
     double g2 = 1.0, g1 = 1.0;  // g eps of l - 1 and l (signed)
     for (int64_t q = 0; q < cstride; ++q) {
-        float2 v = make_float2(0.f, 0.f);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         double sc = 0.0;
         if (q == 0 && len > 0) {
             sc = 1.0;
@@ -201,7 +201,8 @@ __global__ void s2_coef_kernel(int L, int64_t cstride, float2* __restrict__ coef
                                      : -(sqrt((2 * l + 3) / (2 * l - 1)) * (l + 1) * sqrt((l * l - mm) * (l * l - nn)) /
                                          (l * r1)) * g2;
             const double f = g1 / gn;
-            v = make_float2((float)(A * f), (float)(B * f));
+            const float a = (float)(A * f), b = (float)(B * f);
+            v = make_float4(a, a, b, b);
             sc = gn;
             g2 = g1;
             g1 = gn;
@@ -255,15 +256,16 @@ __device__ __forceinline__ void s2_weights(int m, uint32_t thi, uint32_t tlo, fl
     wi = make_float2(g1 * s + g2 * c, g1 * s - g2 * c);
 }
 
-__global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid_constant__ S2Params p) {
+__global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __grid_constant__ S2Params p) {
     extern __shared__ float4 s2_smem[];
     const int L = p.lmax;
     float4* acc = s2_smem;                            // [L + 17] row of the current unit, index l - l0
-    float4* stage = acc + (L + 17);                   // [S2_WARPS][16]
-    float4* xb = stage + S2_WARPS * 16 + (threadIdx.x >> 5) * 16 * S2_XS;  // this warp's [16][S2_XS]
+    float4* stage = acc + (L + 17);                   // [2][S2_WARPS][16], double-buffered
+    float4* xb = stage + 2 * S2_WARPS * 16 + (threadIdx.x >> 5) * 16 * S2_XS;  // this warp's [16][S2_XS]
     // the unit index lives in dynamic shared memory too (no static shared
     // memory, so the launch may use the device's whole opt-in size)
-    int& unit_s = *reinterpret_cast<int*>(stage + S2_WARPS * 16 + S2_WARPS * 16 * S2_XS);
+    int& unit_s = *reinterpret_cast<int*>(stage + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS);
+    int sbuf = 0;  // stage buffer of the next block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = p.ntot;
     const float* X = p.pts;
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
         for (int q = threadIdx.x; q < nblk * 16; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         const float4 sc = p.seedc[m];
-        const float2* coef = p.coef + (int64_t)m * p.cstride;
+        const float4* coef = p.coef + (int64_t)m * p.cstride;
         const double* rowscale = p.scale + (int64_t)m * p.cstride;
         double4* slot = p.slots + (int64_t)ci * p.nmodes + tri_base(m, L) + l0;
         const int nround = ch.n / S2_ROUND;
@@ -317,14 +319,13 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
             bool any_neg = __any_sync(0xffffffffu, lane_neg);
             bool all_dead = __all_sync(0xffffffffu, lane_dead);
             for (int bk = 0; bk < nblk; ++bk) {
-                const float4* cb = reinterpret_cast<const float4*>(coef + bk * 16);  // two steps per float4
+                const float4* cb = coef + bk * 16;
                 const bool skip = all_dead;
                 if (skip) {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c2 = __ldg(cb + (j >> 1));
-                        const float a = (j & 1) ? c2.z : c2.x, b = (j & 1) ? c2.w : c2.y;
-                        const float2 A2 = make_float2(a, a), B2 = make_float2(b, b);
+                        const float4 c = __ldg(cb + j);
+                        const float2 A2 = make_float2(c.x, c.y), B2 = make_float2(c.z, c.w);
 #pragma unroll
                         for (int k = 0; k < S2_K; ++k) {
                             const float2 t = s2_fma2(A2, x2[k], B2);
@@ -336,9 +337,8 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
                 } else {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c2 = __ldg(cb + (j >> 1));
-                        const float a = (j & 1) ? c2.z : c2.x, b = (j & 1) ? c2.w : c2.y;
-                        const float2 A2 = make_float2(a, a), B2 = make_float2(b, b);
+                        const float4 c = __ldg(cb + j);
+                        const float2 A2 = make_float2(c.x, c.y), B2 = make_float2(c.z, c.w);
                         float2 ra = make_float2(0.f, 0.f), ia = ra, rb = ra, ib = ra;
 #pragma unroll
                         for (int k = 0; k < S2_K; ++k) {
@@ -403,32 +403,45 @@ __global__ void __launch_bounds__(S2_WARPS * 32) s2_analysis_kernel(const __grid
                 float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (!skip) {
                     __syncwarp();
+                    // four independent partial sums, then a fixed tree
+                    float4 t4[4];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
+                    for (int c = 0; c < 4; ++c) t4[c] = xb[row * S2_XS + half * 16 + c];
+#pragma unroll
+                    for (int c = 4; c < 16; ++c) {
                         const float4 v = xb[row * S2_XS + half * 16 + c];
-                        s.x += v.x;
-                        s.y += v.y;
-                        s.z += v.z;
-                        s.w += v.w;
+                        t4[c & 3].x += v.x;
+                        t4[c & 3].y += v.y;
+                        t4[c & 3].z += v.z;
+                        t4[c & 3].w += v.w;
                     }
+                    s.x = (t4[0].x + t4[1].x) + (t4[2].x + t4[3].x);
+                    s.y = (t4[0].y + t4[1].y) + (t4[2].y + t4[3].y);
+                    s.z = (t4[0].z + t4[1].z) + (t4[2].z + t4[3].z);
+                    s.w = (t4[0].w + t4[1].w) + (t4[2].w + t4[3].w);
                     s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
                     s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
                     s.z += __shfl_xor_sync(0xffffffffu, s.z, 16);
                     s.w += __shfl_xor_sync(0xffffffffu, s.w, 16);
                     __syncwarp();
                 }
-                if (half == 0) stage[warp * 16 + row] = s;
+                // One barrier per block: the stage is double-buffered, and the
+                // barrier of the next block orders this block's combine before
+                // the buffer is written again.
+                float4* sb = stage + sbuf * S2_WARPS * 16;
+                if (half == 0) sb[warp * 16 + row] = s;
                 __syncthreads();
                 if (threadIdx.x < 64) {
                     const int q = threadIdx.x >> 2, comp = threadIdx.x & 3;
-                    const float* st = reinterpret_cast<const float*>(stage);
+                    const float* st = reinterpret_cast<const float*>(sb);
                     const float v = ((st[(0 * 16 + q) * 4 + comp] + st[(1 * 16 + q) * 4 + comp]) +
                                      st[(2 * 16 + q) * 4 + comp]) + st[(3 * 16 + q) * 4 + comp];
                     reinterpret_cast<float*>(acc)[(bk * 16 + q) * 4 + comp] += v;
                 }
-                __syncthreads();
+                sbuf ^= 1;
             }
             if ((r + 1) % S2_FLUSH == 0 || r + 1 == nround) {
+                __syncthreads();  // the last block's combine is in acc
                 for (int q = threadIdx.x; q < len; q += blockDim.x) {
                     const float4 a = acc[q];
                     const double g = rowscale[q];
@@ -530,7 +543,7 @@ static bool spin2_layout(int L, const S2Catalog* cats, int ncat, int nfield, S2L
     lo.pts_off = b;
     b += s2_up256((size_t)ntot * S2_NARR * 4);
     lo.coef_off = b;
-    b += s2_up256((size_t)(L + 1) * lo.cstride * 8);
+    b += s2_up256((size_t)(L + 1) * lo.cstride * 16);
     lo.scale_off = b;
     b += s2_up256((size_t)(L + 1) * lo.cstride * 8);
     lo.seed_off = b;
@@ -543,7 +556,9 @@ static bool spin2_layout(int L, const S2Catalog* cats, int ncat, int nfield, S2L
     return true;
 }
 
-static size_t spin2_smem_bytes(int L) { return (size_t)(L + 17 + S2_WARPS * 16 + S2_WARPS * 16 * S2_XS + 1) * 16; }
+static size_t spin2_smem_bytes(int L) {
+    return (size_t)(L + 17 + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS + 1) * 16;
+}
 
 static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfield, const S2Layout& lo, char* ws,
                                 unsigned* err, int sm_count, double* E, double* B, cudaStream_t st) {
@@ -575,7 +590,7 @@ static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfie
         s2_prep_kernel<<<dim3((unsigned)bx, ncat + nfield), 256, 0, st>>>(pp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    float2* coef = reinterpret_cast<float2*>(ws + lo.coef_off);
+    float4* coef = reinterpret_cast<float4*>(ws + lo.coef_off);
     double* scale = reinterpret_cast<double*>(ws + lo.scale_off);
     float4* seedc = reinterpret_cast<float4*>(ws + lo.seed_off);
     s2_coef_kernel<<<(L + 1 + 63) / 64, 64, 0, st>>>(L, lo.cstride, coef, scale, seedc);
