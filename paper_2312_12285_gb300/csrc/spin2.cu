@@ -27,7 +27,9 @@
 // two accumulations (re of both spins, im of both spins): four packed f32x2
 // FMAs.
 //
-// Work: a unit is (order m, chunk of points of one field); a CTA of 4 warps
+// Points are laid out per field in |x|-bucket order (as for the scalar
+// path), so warps whose points are all still below the FP32 range skip the
+// accumulation.  Work: a unit is (order m, chunk of points of one field); a CTA of 4 warps
 // takes units from a global counter (largest l-range first).  Each warp runs
 // 256 points (8 per lane) of a round of 1024; per 16 steps a warp reduces its
 // lanes by a shared-memory transpose, the four warps' block sums are added in
@@ -169,6 +171,53 @@ __global__ void s2_prep_kernel(const __grid_constant__ S2PrepParams p) {
         for (int64_t i = i0; i < p.pad_n[f]; i += stride) s2_prep_one(p, p.pad_off[f] + i, 0.f, 0.f, 0.f, 0.f, 0.f, 0.0);
     }
 }
+
+// Points of a field in |x|-bucket order (the scalar path's counting sort:
+// bucket offsets from its hist + scan, then this scatter), so that the 256
+// points of a warp cross into the FP32 range at nearly the same l and whole
+// warps below range skip the accumulation.  The order changes only the
+// summation order; ranks within a bucket follow the input order.
+__global__ void __launch_bounds__(256) s2_scatter_kernel(const __grid_constant__ SortParams sp,
+                                                         const __grid_constant__ S2PrepParams p) {
+    __shared__ int64_t next[SORT_BUCKETS];
+    __shared__ int wcnt[8][SORT_BUCKETS];
+    const int r = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) next[b] = sp.hist[(int64_t)r * SORT_BUCKETS + b];
+    int c = 0;
+    while (c + 1 < sp.prep.ncat && sp.range0[c + 1] <= r) ++c;
+    const int64_t i0 = (int64_t)(r - sp.range0[c]) * SORT_RANGE;
+    const int64_t i1 = min(p.cat[c].n, i0 + SORT_RANGE);
+    __syncthreads();
+    if (i0 >= i1) return;
+    const S2Cat& cd = p.cat[c];
+    for (int64_t base = i0; base < i1; base += 256) {
+        for (int b = lane; b < SORT_BUCKETS; b += 32) wcnt[warp][b] = 0;
+        __syncwarp();
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < i1;
+        const float x = valid ? cd.x[i] : 0.f;
+        const int bk = valid ? x_bucket((double)x) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, bk);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp][bk] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int64_t dst = next[bk] + rank;
+            for (int w = 0; w < warp; ++w) dst += wcnt[w][bk];
+            s2_prep_one(p, dst, x, cd.phi[i], cd.w[i], cd.g1[i], cd.g2[i], cd.coeff);
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < SORT_BUCKETS; b += blockDim.x) {
+            int t = 0;
+            for (int w = 0; w < 8; ++w) t += wcnt[w][b];
+            next[b] += t;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_sort_offsets_f32(const SortParams& sp, cudaStream_t st);  // analysis.cu
 
 // Recurrence coefficients, row scales and seed constants, FP64 (the
 // coefficients then rounded once).  Step q of order m produces tau_{l0+q}:
@@ -496,7 +545,9 @@ struct S2Layout {
     int nchunk = 0;
     S2Chunk chunk[S2_MAXCHUNK];
     int32_t chunk0[PSHT_MAX_FIELDS + 1] = {};
-    size_t pts_off = 0, coef_off = 0, scale_off = 0, seed_off = 0, slots_off = 0, counter_off = 0, total = 0;
+    int64_t nranges = 0;
+    size_t pts_off = 0, hist_off = 0, coef_off = 0, scale_off = 0, seed_off = 0, slots_off = 0, counter_off = 0,
+           total = 0;
 };
 
 static size_t s2_up256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -542,6 +593,9 @@ static bool spin2_layout(int L, const S2Catalog* cats, int ncat, int nfield, S2L
     size_t b = 0;
     lo.pts_off = b;
     b += s2_up256((size_t)ntot * S2_NARR * 4);
+    for (int c = 0; c < ncat; ++c) lo.nranges += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
+    lo.hist_off = b;
+    b += s2_up256((size_t)std::max<int64_t>(lo.nranges, 1) * SORT_BUCKETS * 8);
     lo.coef_off = b;
     b += s2_up256((size_t)(L + 1) * lo.cstride * 16);
     lo.scale_off = b;
@@ -586,9 +640,37 @@ static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfie
             pp.pad_n[f] = lo.npad[f] - lo.nfpts[f];
             nmax = std::max(nmax, pp.pad_n[f]);
         }
+        // padding first (the catalogs' segments of the prep kernel are empty)
+        S2PrepParams* pads = new S2PrepParams(pp);
+        for (int c = 0; c < ncat; ++c) pads->cat[c].n = 0;
         const int64_t bx = std::min<int64_t>((nmax + 255) / 256, 1024);
-        s2_prep_kernel<<<dim3((unsigned)bx, ncat + nfield), 256, 0, st>>>(pp);
+        s2_prep_kernel<<<dim3((unsigned)bx, ncat + nfield), 256, 0, st>>>(*pads);
+        delete pads;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (lo.nranges > 0) {
+            SortParams* sp = new SortParams;
+            memset(sp, 0, sizeof(SortParams));
+            sp->prep.ncat = ncat;
+            sp->prep.nfield = nfield;
+            int64_t r = 0;
+            for (int c = 0; c < ncat; ++c) {
+                sp->prep.cat[c].x = cats[c].x;
+                sp->prep.cat[c].n = cats[c].n;
+                sp->prep.cat[c].field = cats[c].field;
+                sp->range0[c] = r;
+                r += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
+            }
+            sp->range0[ncat] = r;
+            for (int f = 0; f < nfield; ++f) sp->field_off[f] = lo.off[f];
+            sp->hist = reinterpret_cast<int64_t*>(ws + lo.hist_off);
+            e = launch_sort_offsets_f32(*sp, st);
+            if (e == cudaSuccess) {
+                s2_scatter_kernel<<<(unsigned)lo.nranges, 256, 0, st>>>(*sp, pp);
+                e = cudaGetLastError();
+            }
+            delete sp;
+            if (e != cudaSuccess) return e;
+        }
     }
     float4* coef = reinterpret_cast<float4*>(ws + lo.coef_off);
     double* scale = reinterpret_cast<double*>(ws + lo.scale_off);
