@@ -199,7 +199,8 @@ pointsht_status pointsht_cl_backward(int32_t lmax, const double* alm, int32_t nf
 
 /* Bandpowers C_b = sum_l theta_b^l C_l with theta_b^l = 1/Delta_l on
  * [edges[b], edges[b+1]) (Sec. 2.1): cl: device nspec*(lmax+1); edges: device
- * nbin+1 int32 increasing in [0, lmax+1]; out: device nspec*nbin. */
+ * nbin+1 int32 increasing in [0, lmax+1] (clamped into that range on the
+ * device; an empty bin gives 0); out: device nspec*nbin. */
 pointsht_status pointsht_bin(int32_t lmax, const double* cl, int32_t nspec, const int32_t* edges,
                              int32_t nbin, double* out, void* stream);
 

@@ -83,12 +83,20 @@ __global__ void noise_grad_kernel(int L, int nf, const double* __restrict__ gcl,
 }
 
 // Bandpowers C_b = sum_l theta_b^l C_l, theta = 1/Delta_l on [e_b, e_{b+1}) (Sec. 2.1).
+// Bin edges are clamped into [0, L+1] and made non-decreasing on the device,
+// so a malformed edge array cannot send a read or write outside the spectra.
+__device__ __forceinline__ void bin_edges(const int* __restrict__ edges, int b, int L, int& lo, int& hi) {
+    lo = min(max(edges[b], 0), L + 1);
+    hi = min(max(edges[b + 1], lo), L + 1);
+}
+
 __global__ void bin_kernel(int L, const double* __restrict__ cl, int nspec, const int* __restrict__ edges,
                            int nbin, double* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nspec * nbin) return;
     const int s = t / nbin, b = t % nbin;
-    const int lo = edges[b], hi = edges[b + 1];
+    int lo, hi;
+    bin_edges(edges, b, L, lo, hi);
     double acc = 0.0;
     for (int l = lo; l < hi; ++l) acc += cl[(int64_t)s * (L + 1) + l];
     out[t] = hi > lo ? acc / (double)(hi - lo) : 0.0;
@@ -101,7 +109,8 @@ __global__ void bin_backward_kernel(int L, const double* __restrict__ gb, int ns
     const int s = t / (L + 1), l = t % (L + 1);
     double v = 0.0;
     for (int b = 0; b < nbin; ++b) {
-        const int lo = edges[b], hi = edges[b + 1];
+        int lo, hi;
+        bin_edges(edges, b, L, lo, hi);
         if (l >= lo && l < hi) v += gb[(int64_t)s * nbin + b] / (double)(hi - lo);
     }
     gcl[t] = v;
