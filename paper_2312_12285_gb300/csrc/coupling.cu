@@ -77,15 +77,18 @@ __global__ void __launch_bounds__(CP_THREADS) cp_coupling_kernel(int L, int Lw, 
     const double* bl = bs - l;    // bl[g] = b(g - l)
     const double* blp = bs - lp;  // blp[g] = b(g - l'), zero for g < l'
     const double* T = Ts - g0;
-    double acc0 = 0.0, acc1 = 0.0;
+    // four independent accumulators (FP64 latency), combined in a fixed tree
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
     int g = s - wlast;
-    for (; g + 1 <= g1; g += 2) {
+    for (; g + 3 <= g1; g += 4) {
         acc0 = fma(bl[g] * blp[g], T[g], acc0);
         acc1 = fma(bl[g + 1] * blp[g + 1], T[g + 1], acc1);
+        acc2 = fma(bl[g + 2] * blp[g + 2], T[g + 2], acc2);
+        acc3 = fma(bl[g + 3] * blp[g + 3], T[g + 3], acc3);
     }
-    if (g <= g1) acc0 = fma(bl[g] * blp[g], T[g], acc0);
+    for (; g <= g1; ++g) acc0 = fma(bl[g] * blp[g], T[g], acc0);
     if (lraw <= wlast) {
-        const double K = acc0 + acc1;
+        const double K = (acc0 + acc1) + (acc2 + acc3);
         M[(int64_t)l * (L + 1) + lp] = (double)(2 * lp + 1) * K;
         if (lp != l) M[(int64_t)lp * (L + 1) + l] = (double)(2 * l + 1) * K;
     }

@@ -62,3 +62,19 @@ def test_golden_spiral_layout():
     assert np.max(np.abs(dphi)) <= 1e-5
     assert np.array_equal(c.x, catalogs.golden_spiral_workload(4096, 64).catalogs[0].x)
     assert np.all(c.w == 1)
+
+
+def test_coupling_term_count_matches_brute_force():
+    """bench.coupling_terms (the algorithmic work count of the mode-coupling
+    row) against a direct count of the non-zero 3j terms of Eq. chat over
+    pairs l <= l'."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for L, Lw in ((0, 0), (3, 3), (9, 4), (12, 30), (20, 20)):
+        n = sum(1 for l in range(L + 1) for lp in range(l, L + 1)
+                for lam in range(lp - l, min(l + lp, Lw) + 1) if (l + lp + lam) % 2 == 0)
+        assert bench.coupling_terms(L, Lw) == n, (L, Lw)
