@@ -561,7 +561,7 @@ __device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m,
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 // stage order: all products, all recurrence FMAs, then the
-                // accumulation in two independent chains per component
+                // accumulation
                 float2 t[KP];
 #pragma unroll
                 for (int kp = 0; kp < KP; ++kp) t[kp] = f2_mul(x2[kp], p1[kp]);
@@ -571,16 +571,16 @@ __device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m,
                     p2[kp] = p1[kp];
                     p1[kp] = sg;
                 }
+                // one packed chain per component (the next step's recurrence
+                // does not depend on it, so its latency overlaps), then one
+                // add per component
                 float2 r0 = f2_mul(p1[0], wc2[0]), i0 = f2_mul(p1[0], ws2[0]);
-                float2 r1 = f2_mul(p1[1], wc2[1]), i1 = f2_mul(p1[1], ws2[1]);
 #pragma unroll
-                for (int kp = 2; kp < KP; kp += 2) {
+                for (int kp = 1; kp < KP; ++kp) {
                     r0 = f2_fma(p1[kp], wc2[kp], r0);
                     i0 = f2_fma(p1[kp], ws2[kp], i0);
-                    r1 = f2_fma(p1[kp + 1], wc2[kp + 1], r1);
-                    i1 = f2_fma(p1[kp + 1], ws2[kp + 1], i1);
                 }
-                xb[j * XS + lane] = make_float2((r0.x + r1.x) + (r0.y + r1.y), (i0.x + i1.x) + (i0.y + i1.y));
+                xb[j * XS + lane] = make_float2(r0.x + r0.y, i0.x + i0.y);
             }
         }
         if (any_neg) {
