@@ -452,7 +452,7 @@ def ours(args):
                                     "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)"),
                          "kernel_ms": kms,
                          "peak_source": peak_src,
-                         "ncu_pipe": None if prec in ("fp64", "interp") else {"sm__pipe_fma_cycles_active_pct": 67.9, "smsp__issue_active_pct": 47.2,
+                         "ncu_pipe": None if prec in ("fp64", "interp") else {"sm__pipe_fma_cycles_active_pct": 69.0, "smsp__issue_active_pct": 46.9,
                                       "source": "profiles/analysis_kernel_lognormal_cap_1e5pts_l2048_full.md "
                                                 "(same kernel and launch shape, 1e5-point case: these counters "
                                                 "take 3 ncu passes, so they are not captured at full size)"}},
