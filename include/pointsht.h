@@ -219,7 +219,11 @@ pointsht_status pointsht_bin_backward(int32_t lmax, const double* grad_b, int32_
  * This is a point-evaluation synthesis that reruns the recurrence per point
  * (derived from Eq. alm_def; the paper has no adjoint).  grad_w: HOST array of
  * ncat device pointers, each n_c values of the dtype of w (may alias nothing
- * else).  workspace as for pointsht_alm (pointsht_workspace_size bytes). */
+ * else).  workspace as for pointsht_alm (pointsht_workspace_size bytes).
+ * FP32 (and MIXED, which runs as FP32): the points are prepared and
+ * |x|-sorted as for the analysis, each keeping its id, so the total number
+ * of points must be below 2^32 - 1 (EINVAL otherwise); lmax <= the FP32
+ * path's limit.  FP64: catalog order. */
 pointsht_status pointsht_alm_backward(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
                                       int32_t nfield, pointsht_precision prec, const double* grad_alm,
                                       const double* grad_noise, void* const* grad_w, void* workspace,
