@@ -19,7 +19,6 @@ summed with one NCCL all-reduce (the sum over points is the only exchange).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import math
 import os
@@ -56,6 +55,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-coupling", action="store_true", help="skip the mode-coupling matrix measurement")
     ap.add_argument("--no-spin2", action="store_true", help="skip the spin-2 (shear) transform measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batching workload (16 tomographic bins + shared randoms, lmax 1536)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = automatic)")
@@ -116,32 +117,6 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- helpers --
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("analysis.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2312_12285_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
-
-
-def profiled_traffic(workload: str, npoints: int):
-    """DRAM bytes per launch of the analysis kernel from the committed ncu
-    summary (profiles/analysis_kernel_lognormal_cap_l2048_traffic.md), scaled
-    to this launch's points; None if absent, for another workload, or if the
-    kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "analysis_kernel_lognormal_cap_l2048_traffic.md")
-    try:
-        kv = {}
-        for line in open(path):
-            if ":" in line and not line.startswith(("|", " ", "#")):
-                k, v = line.split(":", 1)
-                kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_hash") != kernel_source_hash() or workload != "lognormal_cap_l2048":
-            return None
-        return float(kv["dram_bytes_per_launch"]) / float(kv["points"]) * npoints
-    except Exception:
-        return None
-
-
 def load_workload(args):
     from paper_2312_12285_gb300 import catalogs
     wl = catalogs.config(args.config, scale=args.scale, lmax=args.lmax)
@@ -264,7 +239,7 @@ def ours(args):
     nout = nfield if coef is None else coef.shape[0]
 
     if prec == "interp":
-        nt = ops.default_ntheta(L)
+        nt = ops.ntheta_for_tolerance(L, 1e-4)
         ws = torch.empty(max(ws.numel(), ops.workspace_bytes_interp(plan, cats, nfield, nt)), dtype=torch.uint8,
                          device=dev)
 
@@ -352,7 +327,6 @@ def ours(args):
         # (4 spline weights x complex MAC, phase rotation), transform of the
         # samples 27 per (sample, mode) (recurrence, 6 columns x complex MAC)
         achieved = (22.0 * n_rank * (L + 1) + 27.0 * nt * wl.nmodes) / (kms / 1e3) / 1e12
-    traffic = profiled_traffic(wl.name, n_rank) if prec == "fp32" else None
 
     # ---- end to end through the public API, host buffers in pinned memory ----
     e2e = None
@@ -426,6 +400,22 @@ def ours(args):
     spin2 = None
     if rank == 0 and world == 1 and not args.no_spin2 and prec == "fp32" and coef is None:
         spin2 = spin2_measure(plan, wl, dev, L, peak, peak_src)
+    skipped = None
+    if prec == "fp32" and coef is None:
+        # fraction of (point, m, l) accumulation steps skipped below the FP32 range (one untimed call)
+        cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+        plan.set_skip_counters(cnt)
+        ops.alm_raw(plan, cats, nfield, prec, out=out, workspace=ws)
+        torch.cuda.synchronize()
+        plan.set_skip_counters(None)
+        plan.check()
+        c = cnt.cpu().tolist()
+        skipped = {"fraction": c[0] / max(1, c[1]), "blocks_skipped": c[0], "blocks": c[1],
+                   "what": "16-step recurrence blocks of a warp whose points were all below the FP32 range: "
+                           "accumulation not executed (exact zeros), counted by the kernel"}
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched and prec == "fp32" and args.config == 3:
+        batched = batched_measure(dev, peak, peak_src)
     ladder = None
     if rank == 0 and world == 1 and not args.no_ladder and prec == "fp32" and wl.nfield == 1:
         ladder = precision_ladder(wl, plan, dev, value, accuracy["cl_err_vs_fp64_oracle"] if accuracy else None,
@@ -441,21 +431,19 @@ def ours(args):
                        "fields": nfield, "l2": "inputs larger than L2 (prepared points 24 B x 1e7 = 240 MB)",
                        "modes_counted": "nominal (lmax+1)(lmax+2)/2 per point; accumulation skipped in 16-step "
                                         "blocks where every point of a warp is below the FP32 range (exact zeros)",
+                       "accumulation_skipped": skipped,
                        "parallelism": f"points sharded over {world} GPU(s), one all-reduce of a_lm",
                        "cuda_graph": bool(gstep is not None)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak,
+                         "traffic": None,  # DRAM bytes come from an ncu capture, not from this run
                          "kernel": ("analysis_kernel (FP64, 4 points/lane, 4 warps/CTA)" if prec == "fp64" else
                                     "interpolated route: sort, ip_bin, ip_fold, analysis_mixed_kernel<8> table "
                                     "mode, combine (timed together; algorithmic flops against the FP32 peak)"
                                     if prec == "interp" else
                                     "analysis_kernel (FP32, 16 points/lane in f32x2 pairs, 4 warps/CTA)"),
                          "kernel_ms": kms,
-                         "peak_source": peak_src,
-                         "ncu_pipe": None if prec in ("fp64", "interp") else {"sm__pipe_fma_cycles_active_pct": 69.0, "smsp__issue_active_pct": 46.9,
-                                      "source": "profiles/analysis_kernel_lognormal_cap_1e5pts_l2048_full.md "
-                                                "(same kernel and launch shape, 1e5-point case: these counters "
-                                                "take 3 ncu passes, so they are not captured at full size)"}},
+                         "peak_source": peak_src},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
@@ -465,6 +453,7 @@ def ours(args):
             "adjoint": adjoint,
             "coupling": coupling,
             "spin2": spin2,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -647,6 +636,146 @@ def time_columns(plan, xd, pd, Wd, prec, reps, warm=1):
     return e0.elapsed_time(e1) / reps, sum(a.elapsed_time(b) for a, b in evk) / reps, out
 
 
+def batched_measure(dev, peak, peak_src, steps_fp32=2, steps_interp=5, cpu_pm=1.0e10):
+    """The batching workload: 16 tomographic bins of uneven sizes (10^U[5,7]
+    galaxies) plus 2e7 shared randoms, lmax 1536, all 17 source fields in one
+    call, combined into the 16 FKP fields D_b - alpha_b R (Sec. 2.1), all 136
+    auto and cross pseudo-C_l with shot noise removed.  Timed through the plain
+    FP32 path (the whole step captured in one CUDA graph) and through the
+    interpolated route (tensor-core contraction of theta-sample tables,
+    ntheta from the 1e-4 C_l budget); each with its device time, an end-to-end
+    time through the public API with host buffers, its roofline, and its C_l
+    error against the FP64 oracle on a bounded sample of the workload."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2312_12285_gb300 import catalogs, ops
+    wl = catalogs.config(4)
+    L, M = wl.lmax, wl.nmodes
+    nb = wl.extra["nbins"]
+    nsrc = wl.nfield
+    cm = np.zeros((nb, nsrc))
+    for b in range(nb):
+        cm[b, b] = 1.0
+        cm[b, nb] = -wl.extra["alpha"][b]
+    coef = torch.from_numpy(cm).to(dev)
+    host = [tuple(torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in (c.x, c.phi, c.w))
+            for c in wl.catalogs]
+    cats = [ops.Cat(h[0].to(dev), h[1].to(dev), h[2].to(dev), c.field, c.coeff) for h, c in zip(host, wl.catalogs)]
+    plan = ops.get_plan(L, dev)
+    h2d = sum(sum(t.numel() * t.element_size() for t in h) for h in host)
+    npair = nb * (nb + 1) // 2
+    cl_h = torch.empty((npair, L + 1), dtype=torch.float64).pin_memory()
+    total_pm = wl.npoints * M
+    res = {"workload": f"tomographic: 16 bins ({min(c.n for c in wl.catalogs[:nb])}..{max(c.n for c in wl.catalogs[:nb])} "
+                       f"galaxies) + 2e7 shared randoms = {wl.npoints} points, lmax {L}, 17 source fields -> "
+                       f"{nb} FKP fields, {npair} spectra",
+           "points": wl.npoints, "lmax": L, "unit": UNIT}
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        return e0.elapsed_time(e1) / steps
+
+    # ---- plain FP32 path, one CUDA graph per step ----
+    step = ops.GraphStep(ops.make_pipeline(plan, cats, nsrc, "fp32", coef=coef), warmup=1)
+    ms = timed(step.replay, steps_fp32)
+    dcats = [ops.Cat(torch.empty_like(c.x), torch.empty_like(c.phi), torch.empty_like(c.w), c.field, c.coeff)
+             for c in cats]
+    fn_e2e = ops.make_pipeline(plan, dcats, nsrc, "fp32", coef=coef)
+
+    def e2e_fp32():
+        for h, d in zip(host, dcats):
+            d.x.copy_(h[0], non_blocking=True)
+            d.phi.copy_(h[1], non_blocking=True)
+            d.w.copy_(h[2], non_blocking=True)
+        cl_h.copy_(fn_e2e()[0], non_blocking=True)
+    ems = timed(e2e_fp32, 1)
+    del fn_e2e
+    ach = FLOPS_PER_POINT_MODE * total_pm / (ms / 1e3) / 1e12
+    res["fp32"] = {"value": total_pm / (ms / 1e3), "ms_per_step": ms,
+                   "e2e": {"value": total_pm / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                           "d2h_bytes_per_step": int(cl_h.numel() * 8), "ms_per_step": ems},
+                   "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                "traffic": None, "peak_source": peak_src,
+                                "kernel": "analysis_kernel (FP32, one persistent launch over all 17 fields), "
+                                          "timed as the whole graph step"},
+                   "gpu_launches_per_step": 12}
+    del step
+    # ---- interpolated route ----
+    nt = ops.ntheta_for_tolerance(L, 1e-4)
+    wsi = torch.empty(ops.workspace_bytes_interp(plan, cats, nsrc, nt), dtype=torch.uint8, device=dev)
+    outi = torch.empty((nsrc, plan.nmodes), dtype=torch.complex128, device=dev)
+    nws = torch.empty(512 * len(cats) + 256, dtype=torch.uint8, device=dev)
+
+    def istep(cs=cats):
+        a = ops.alm_interp(plan, cs, nsrc, nt, out=outi, workspace=wsi)
+        noise = ops.shot_noise_raw(cs, nsrc, "fp32", dev, workspace=nws)
+        af, nf = ops.combine_raw(a, coef, noise)
+        return ops.cl_raw(af, nf)
+    ims = timed(istep, steps_interp)
+
+    def e2e_interp():
+        for h, d in zip(host, dcats):
+            d.x.copy_(h[0], non_blocking=True)
+            d.phi.copy_(h[1], non_blocking=True)
+            d.w.copy_(h[2], non_blocking=True)
+        cl_h.copy_(istep(dcats), non_blocking=True)
+    iems = timed(e2e_interp, steps_interp)
+    iach = (22.0 * wl.npoints * (L + 1) + 27.0 * nt * M * nsrc) / (ims / 1e3) / 1e12
+    res["interp"] = {"value": total_pm / (ims / 1e3), "ms_per_step": ims, "ntheta": nt,
+                     "ntheta_rule": "smallest even N with 4.3e-6 (16 lmax / N)^4 <= 1e-4 / 4 (h^4 model)",
+                     "e2e": {"value": total_pm / (iems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                             "d2h_bytes_per_step": int(cl_h.numel() * 8), "ms_per_step": iems},
+                     "roofline": {"bound": "alu", "achieved": iach, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": iach / peak, "traffic": None, "peak_source": peak_src,
+                                  "kernel": "interpolated route (sort, ip_bin, ip_fold, analysis_mixed_kernel<8> "
+                                            "table mode per field, reduce, combine), algorithmic flops: 22 per "
+                                            "(point, m) binning + 27 per (sample, mode) per field"}}
+    res["interp_speedup_vs_fp32"] = res["interp"]["value"] / res["fp32"]["value"]
+    del wsi, outi, dcats
+    # ---- C_l error of both routes against the FP64 oracle on a bounded sample ----
+    sample = oracle_sample(wl, cpu_pm)
+    t0 = time.perf_counter()
+    ref = [oracle.alm(x, p, w.astype(np.float64), L) for (x, p, w, co, f) in sample]
+    cpu_s = time.perf_counter() - t0
+    scats = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (x, p, w)), f, co)
+             for (x, p, w, co, f) in sample]
+    alpha = wl.extra["alpha"]
+    fk = [ref[b] - alpha[b] * ref[nb] for b in range(nb)]
+    tot = [oracle.cl(fk[b], fk[b], L) for b in range(nb)]
+    noise_s = ops.shot_noise_raw(scats, nsrc, "fp32", dev)
+
+    def cl_err(a_src):
+        af, nf = ops.combine_raw(a_src, coef, noise_s)
+        cl = ops.cl_raw(af, nf).cpu().numpy()
+        nfh = nf.cpu().numpy()
+        worst, p_ = 0.0, 0
+        for f in range(nb):
+            for g in range(f, nb):
+                want = oracle.cl(fk[f], fk[g], L) - nfh[f, g]
+                worst = max(worst, float(np.max(np.abs(cl[p_][1:] - want[1:]) / np.sqrt(tot[f][1:] * tot[g][1:]))))
+                p_ += 1
+        return worst
+    res["fp32"]["cl_err_vs_fp64_oracle"] = cl_err(ops.alm_raw(plan, scats, nsrc, "fp32"))
+    res["interp"]["cl_err_vs_fp64_oracle"] = cl_err(ops.alm_interp(plan, scats, nsrc, nt))
+    plan.check()
+    npts = sum(s[0].shape[0] for s in sample)
+    res["cl_err_definition"] = ("max over the 136 pairs (f, g) and 1 <= l <= lmax of |C_l^fg - ref| / "
+                                "sqrt(C_l^ff C_l^gg) (totals before shot-noise subtraction)")
+    res["oracle_sample"] = f"first {npts} points of every catalog in proportion, all {M} modes, {cpu_s:.1f} s"
+    del cats, host
+    return res
+
+
 def precision_ladder(wl, plan, dev, fp32_value, fp32_cl_err, sample):
     """Mixed path for F = 1, 4, 8 weight columns on the workload's point set
     (per-column throughput, speed-up over the plain FP32 path at the same F,
@@ -694,7 +823,7 @@ def precision_ladder(wl, plan, dev, fp32_value, fp32_cl_err, sample):
     # interpolated route (App. "Interpolation", samples in theta), whole workload
     cats = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (c.x, c.phi, c.w)), c.field,
                     c.coeff) for c in wl.catalogs]
-    nt = ops.default_ntheta(L)
+    nt = ops.ntheta_for_tolerance(L, 1e-4)
     wsi = torch.empty(ops.workspace_bytes_interp(plan, cats, wl.nfield, nt), dtype=torch.uint8, device=dev)
     outi = ops.alm_interp(plan, cats, wl.nfield, nt, workspace=wsi)
     torch.cuda.synchronize()
@@ -910,8 +1039,29 @@ def ours_columns(args):
         dist.destroy_process_group()
 
 
+def spawn_ranks(args) -> int:
+    """--gpus N > 1 outside torchrun: start N ranks on this node, one per GPU
+    (torch.distributed.run, rendezvous on 127.0.0.1), and return their exit
+    status; an error if this node has fewer than N GPUs."""
+    import socket
+
+    import torch
+    if torch.cuda.device_count() < args.gpus:
+        print(json.dumps({"error": f"--gpus {args.gpus}: this node has {torch.cuda.device_count()} GPU(s)"}),
+              flush=True)
+        return 2
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args))
     if args.impl == "reference":
         reference_arm(args)
     elif args.columns > 0 or args.precision == "mixed":

@@ -133,11 +133,46 @@ pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start,
 /* Tuning of the FP32 analysis kernel for this plan (the paper has no
  * counterpart; chosen by the autotuner): variant 0 = library default, or
  * 8 / 12 / 16 = points per lane with scalar FMAs, 116 = 16 points per lane as
- * f32x2 pairs, 108 = four warps sharing each order pair's accumulator;
+ * f32x2 pairs, 118 = 116 with the accumulator rows in global memory (three
+ * CTAs per SM), 108 = four warps sharing each order pair's accumulator (only
+ * 116 and 118 carry the near-pole form, pointsht_plan_set_pole_threshold);
  * chunk_log2 0 = automatic, else log2 of the points per accumulation chunk
  * (10..22).  Changes the workspace size: query pointsht_workspace_size after
  * setting.  EINVAL for values outside these sets. */
 pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, int32_t chunk_log2);
+
+/* Accuracy near the poles (App. A recurrence, read numerically; the paper
+ * does not discuss it).  Near x = +-1 the three-term recurrence in l has a
+ * double root and FP32 rounding grows like l^1.5 eps there.  In the FP32
+ * analysis (default variant) and the FP32 adjoint / synthesis, a tile (warp)
+ * of points that all have x >= pole_x, or all x <= -pole_x, runs the
+ * recurrence in Reinsch's difference form on |x| (relative error ~1e-6 of
+ * the column maximum up to lmax 2048 at any x, instead of up to ~5e-3 at
+ * theta ~ 1e-3): one more packed FP32 operation per point and step.  Default
+ * 0.9; a value above 1 turns the form off.  EINVAL for values below 0.5 or NaN
+ * (the form is less accurate than the standard one near x = 0). */
+pointsht_status pointsht_plan_set_pole_threshold(pointsht_plan plan, float pole_x);
+
+/* Measurement hook (the paper has no counterpart): while counters is not
+ * NULL, every FP32 analysis launch of variant 116 / 118 adds to the device
+ * array counters[2] (uint64, caller-owned, zeroed by the caller) the number of
+ * 16-step recurrence blocks (times the warp's points) whose accumulation was
+ * skipped because every point of the warp was still below the FP32 range
+ * ([0]) and the number of all such blocks ([1]).  Their ratio is the fraction
+ * of nominal (point, m, l) accumulation steps not executed (they contribute
+ * exact zeros).  NULL turns it off.  EINVAL if counters is not 8-byte
+ * aligned. */
+pointsht_status pointsht_plan_set_skip_counters(pointsht_plan plan, void* counters);
+
+/* Test hook of the bounded waits (the paper has no counterpart).  While
+ * enabled, the first CTA of each FP32/FP64 analysis launch waits, bounded, on
+ * a shared-memory barrier that no copy and no thread ever arrives at; the
+ * wait gives up, the CTA records the timeout in the plan's error word and
+ * leaves before it takes a work unit or issues a copy (the other CTAs take
+ * every unit, so the a_lm are still complete when the launch has more than
+ * one CTA).  The next pointsht_plan_check returns POINTSHT_ETIMEOUT.  Never
+ * faults or hangs: nothing is left in flight. */
+pointsht_status pointsht_plan_set_wait_probe(pointsht_plan plan, int32_t enable);
 
 /* Bytes of device workspace pointsht_alm / pointsht_alm_backward need for
  * this set of catalogs (host array cats[ncat]; only n and field are read).
@@ -404,7 +439,11 @@ pointsht_status pointsht_fkp_normalise(int32_t lmax_w, const double* W, int32_t 
  *   for these catalogs exceeds POINTSHT_NOALLOC_SCRATCH_BYTES (roughly lmax
  *   <= 512 with up to ~1e6 points; larger problems need pointsht_alm).
  * - The first call on a device looks up the array's device address on that
- *   device (make it before any stream capture); later calls reuse it.
+ *   device; with CUDA's lazy module loading that lookup is also what loads the
+ *   library's device code, and the array with it, onto that device.  Callers
+ *   that must not see any allocation once running should make one warm-up
+ *   call on each device first (and before any stream capture); later calls
+ *   reuse the address and allocate nothing.
  * - All calls share the one array and it keeps the last call's contents;
  *   everything the transform needs to start at zero is cleared by the call.
  *   Calls whose work overlaps on the GPU (different streams, or different host

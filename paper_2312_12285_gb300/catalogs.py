@@ -457,7 +457,7 @@ def _config(i: int, scale: float, lmax: int | None) -> Workload:
 def _cache_dir() -> str:
     d = os.environ.get("POINTSHT_CACHE_DIR")
     if not d:
-        d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), ".cache", "catalogs")
+        d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_cache", "catalogs")
     return d
 
 

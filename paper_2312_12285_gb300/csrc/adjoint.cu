@@ -224,6 +224,13 @@ __device__ __forceinline__ float2 adj_fma2(float2 a, float2 b, float2 c) {
           "l"(reinterpret_cast<unsigned long long&>(c)));
     return d;
 }
+__device__ __forceinline__ float2 adj_add2(float2 a, float2 b) {
+    float2 d;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
 __device__ __forceinline__ float2 adj_mul2(float2 a, float2 b) {
     float2 d;
     asm("mul.rn.f32x2 %0, %1, %2;"
@@ -273,9 +280,32 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
         tot[k] = 0.0;
     }
     const float4* gtab = static_cast<const float4*>(p.gtab) + (int64_t)f * p.gstride;
+    // Near a pole (every point of the warp at x >= pole_x, or every point at
+    // x <= -pole_x) and for m < pole_mmax the recurrence runs in the
+    // analysis's near-pole form (column_f32x2_pole): Reinsch's difference form
+    // of the unfolded recurrence on |x|, with p1 = y_{q-1}, p2 = d_{q-1}, and
+    // the factor s_q sgn^q (q odd ? rho_m : 1) of sigma_q applied to the
+    // table entry of step j.
+    // (padding points do not count: their gradient is not written)
+    bool np = true, sp = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float xv = (k & 1) ? x2[k >> 1].y : x2[k >> 1].x;
+        const bool idle = tu[6 * N + start + 32 * k + lane] == 0xffffffffu;
+        np &= idle | (xv >= p.pole_x);
+        sp &= idle | (xv <= -p.pole_x);
+    }
+    const float sgn = __all_sync(0xffffffffu, np) ? 1.f : (__all_sync(0xffffffffu, sp) ? -1.f : 0.f);
+    const bool pole = sgn != 0.f;
+    float2 u2[KP];
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp) u2[kp] = make_float2(fabsf(x2[kp].x) - 1.f, fabsf(x2[kp].y) - 1.f);
 
     for (int m = 0; m <= L; ++m) {
         const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
+        const bool pole_m = pole && m < p.pole_mmax;
+        const float sr = pole_m ? sgn * p.pole_rho[m] : 0.f;
+        const float sj[4] = {1.f, sr, -1.f, -sr};  // s_q sgn^q (q odd ? rho : 1), q = j (mod 4)
         float2 p1[KP], p2[KP], ar[KP], ai[KP];
         float cs[K], sn[K];
         int E[K];
@@ -303,14 +333,42 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
         const float2* al = p.alpha2 + cs0;
         const float4* gc = gtab + cs0;
         const int nblk = (L - m + 1 + 7) >> 3;
+        const float4* pa = p.pole_ae + cs0;
         for (int bk = 0; bk < nblk; ++bk) {
-            float2 av[8];
+            if (pole_m) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float4 cv[4], gq[4];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        cv[jj] = __ldg(pa + 8 * bk + 4 * h + jj);
+                        gq[jj] = __ldg(gc + 8 * bk + 4 * h + jj);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const float2 a2 = make_float2(cv[jj].x, cv[jj].y), e2 = make_float2(cv[jj].z, cv[jj].w);
+                        const float s = sj[jj];  // q = 8 bk + 4 h + jj = jj (mod 4)
+                        const float2 gr = make_float2(s * gq[jj].x, s * gq[jj].y);
+                        const float2 gi = make_float2(s * gq[jj].z, s * gq[jj].w);
+#pragma unroll
+                        for (int kp = 0; kp < KP; ++kp) {
+                            const float2 c = adj_fma2(a2, u2[kp], e2);
+                            p2[kp] = adj_fma2(c, p1[kp], p2[kp]);
+                            p1[kp] = adj_add2(p1[kp], p2[kp]);
+                            if (!all_dead) {
+                                ar[kp] = adj_fma2(p1[kp], gr, ar[kp]);
+                                ai[kp] = adj_fma2(p1[kp], gi, ai[kp]);
+                            }
+                        }
+                    }
+                }
+            } else {
             float4 gv[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                av[j] = __ldg(al + 8 * bk + j);
-                gv[j] = __ldg(gc + 8 * bk + j);
-            }
+            for (int j = 0; j < 8; ++j) gv[j] = __ldg(gc + 8 * bk + j);
+            float2 av[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) av[j] = __ldg(al + 8 * bk + j);
             if (all_dead) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
@@ -331,6 +389,7 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
                         ar[kp] = adj_fma2(mu, make_float2(gv[j].x, gv[j].y), ar[kp]);
                         ai[kp] = adj_fma2(mu, make_float2(gv[j].z, gv[j].w), ai[kp]);
                     }
+            }
             }
             if (any_neg) {
                 // rescale check every 8 steps (F32Scale; 8-step growth <= 2^42)

@@ -490,12 +490,37 @@ __device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
     return d;
 }
 
+// Per-warp FP32 accumulator rows in global memory (variant 118).  Entry q of
+// a column is updated only by lane q mod 16 of the warp that owns the row, by
+// a fire-and-forget atomic add at device scope (performed in L2, in that
+// lane's program order, so the sum is the same bit for bit on every run); the
+// same lane reads and clears it with device-scope loads and stores, which are
+// ordered after its own adds.
+__device__ __forceinline__ void gacc_add(float2* p, float a, float b) { atomicAdd(p, make_float2(a, b)); }
+__device__ __forceinline__ float2 gacc_take(float2* p) {
+    float2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(0.f), "f"(0.f) : "memory");
+    return v;
+}
+__device__ __forceinline__ void gacc_clear(float2* p) {
+    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(0.f), "f"(0.f) : "memory");
+}
+
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    float2 d;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
+
 __device__ __forceinline__ bool needs_rescale(int E, float a, float b) {
     return (E < 0) & (fmaxf(fabsf(a), fabsf(b)) > TraitsF32::thresh());
 }
 
 template <int K>
-__device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m, int L,
+__device__ __forceinline__ int column_f32x2(const uint32_t* tile, int P, int m, int L,
                                              const float2* __restrict__ alpha2, float lch, float lcl, float2* acc,
                                              float2* xb, int lane) {
     constexpr int KP = K / 2;
@@ -523,6 +548,7 @@ __device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m,
     bool any_neg = __any_sync(0xffffffffu, lane_neg);
     bool all_dead = __all_sync(0xffffffffu, lane_dead);
 
+    int nskip = 0;  // blocks of 16 steps whose accumulation was skipped
     const int nblk = (len + 15) >> 4;
     // coefficients of the next block are fetched while the current one runs
     float4 an[8];
@@ -543,7 +569,8 @@ __device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m,
 #pragma unroll
             for (int c = 0; c < 8; ++c) an[c] = __ldg(a4 + c);
         }
-        const bool skip = all_dead;  // decided for this whole block of 16 steps
+        const bool skip = all_dead;
+        nskip += skip;  // decided for this whole block of 16 steps
         if (skip) {  // every point of the warp is still below range: recurrence only
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -639,6 +666,318 @@ __device__ __forceinline__ void column_f32x2(const uint32_t* tile, int P, int m,
             __syncwarp();
         }
     }
+    return nskip;
+}
+
+
+// ---------------------------------------------------------------------
+// FP32 column, variants 118-124: the arithmetic of column_f32x2, with the
+// coefficients fetched four steps at a time (one group ahead) instead of a
+// whole block ahead (fewer registers), the accumulator row in shared memory
+// or in global memory (GACC: gacc_add; a CTA then needs far less shared
+// memory), and the accumulation over the lane's pairs in CH = 1 or 2 chains
+// per component (two halve the dependency chain, for one packed add more).
+// ---------------------------------------------------------------------
+template <int K, bool GACC, int CH>
+__device__ __forceinline__ int column_f32x2v(const uint32_t* tile, int P, int m, int L,
+                                               const float2* __restrict__ alpha2, float lch, float lcl, float2* acc,
+                                               float2* xb, int lane) {
+    constexpr int KP = K / 2;
+    constexpr int XS = TraitsF32::XSTRIDE;
+    const int len = L - m + 1;
+    float2 x2[KP], p1[KP], p2[KP], wc2[KP], ws2[KP];
+    int E[K];
+    bool lane_neg = false, lane_dead = true;
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp) {
+        float xv[2], mant[2], cs[2], sn[2], w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * kp + h;
+            TraitsF32::setup(tile, P, k * 32 + lane, m, lch, lcl, xv[h], mant[h], E[k], cs[h], sn[h], w[h]);
+            lane_neg |= E[k] != 0;
+            lane_dead &= E[k] != 0;
+        }
+        x2[kp] = make_float2(xv[0], xv[1]);
+        p1[kp] = make_float2(0.f, 0.f);          // sigma_{m-1}
+        p2[kp] = make_float2(mant[0], mant[1]);  // sigma_{m-2}
+        wc2[kp] = make_float2(E[2 * kp] == 0 ? w[0] * cs[0] : 0.f, E[2 * kp + 1] == 0 ? w[1] * cs[1] : 0.f);
+        ws2[kp] = make_float2(E[2 * kp] == 0 ? -w[0] * sn[0] : 0.f, E[2 * kp + 1] == 0 ? -w[1] * sn[1] : 0.f);
+    }
+    bool any_neg = __any_sync(0xffffffffu, lane_neg);
+    bool all_dead = __all_sync(0xffffffffu, lane_dead);
+
+    int nskip = 0;  // blocks of 16 steps whose accumulation was skipped
+    const int nblk = (len + 15) >> 4;
+    // float4 i holds the pairs (alpha_{2i}, alpha_{2i}), (alpha_{2i+1}, alpha_{2i+1});
+    // a group of four steps is two of them.  The group after the column's last
+    // lies in the next column or in the 32 zero entries after the last one.
+    const float4* a4 = reinterpret_cast<const float4*>(alpha2);
+    float4 n0 = __ldg(a4), n1 = __ldg(a4 + 1);
+    for (int bk = 0; bk < nblk; ++bk) {
+        const bool skip = all_dead;
+        nskip += skip;  // decided for this whole block of 16 steps
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const float2 av[4] = {make_float2(n0.x, n0.y), make_float2(n0.z, n0.w), make_float2(n1.x, n1.y),
+                                  make_float2(n1.z, n1.w)};
+            n0 = __ldg(a4 + 8 * bk + 2 * g + 2);
+            n1 = __ldg(a4 + 8 * bk + 2 * g + 3);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * g + jj;
+                float2 t[KP];
+#pragma unroll
+                for (int kp = 0; kp < KP; ++kp) t[kp] = f2_mul(x2[kp], p1[kp]);
+#pragma unroll
+                for (int kp = 0; kp < KP; ++kp) {
+                    const float2 sg = f2_fma(av[jj], t[kp], p2[kp]);
+                    p2[kp] = p1[kp];
+                    p1[kp] = sg;
+                }
+                if (!skip) {
+                    if constexpr (CH == 1) {
+                        float2 r0 = f2_mul(p1[0], wc2[0]), i0 = f2_mul(p1[0], ws2[0]);
+#pragma unroll
+                        for (int kp = 1; kp < KP; ++kp) {
+                            r0 = f2_fma(p1[kp], wc2[kp], r0);
+                            i0 = f2_fma(p1[kp], ws2[kp], i0);
+                        }
+                        xb[j * XS + lane] = make_float2(r0.x + r0.y, i0.x + i0.y);
+                    } else {
+                        constexpr int H = KP / 2;
+                        float2 r0 = f2_mul(p1[0], wc2[0]), i0 = f2_mul(p1[0], ws2[0]);
+                        float2 r1 = f2_mul(p1[H], wc2[H]), i1 = f2_mul(p1[H], ws2[H]);
+#pragma unroll
+                        for (int kp = 1; kp < H; ++kp) {
+                            r0 = f2_fma(p1[kp], wc2[kp], r0);
+                            i0 = f2_fma(p1[kp], ws2[kp], i0);
+                            r1 = f2_fma(p1[H + kp], wc2[H + kp], r1);
+                            i1 = f2_fma(p1[H + kp], ws2[H + kp], i1);
+                        }
+                        r0 = f2_add(r0, r1);
+                        i0 = f2_add(i0, i1);
+                        xb[j * XS + lane] = make_float2(r0.x + r0.y, i0.x + i0.y);
+                    }
+                }
+            }
+        }
+        if (any_neg) {
+            // rescale check once per 16 steps (as column_f32x2)
+            bool reached = false;
+            lane_neg = false;
+            lane_dead = true;
+#pragma unroll
+            for (int kp = 0; kp < KP; ++kp) {
+                const bool nx = needs_rescale(E[2 * kp], p1[kp].x, p2[kp].x);
+                const bool ny = needs_rescale(E[2 * kp + 1], p1[kp].y, p2[kp].y);
+                const float2 f = make_float2(nx ? 0x1p-64f : 1.f, ny ? 0x1p-64f : 1.f);
+                p1[kp] = f2_mul(p1[kp], f);
+                p2[kp] = f2_mul(p2[kp], f);
+                E[2 * kp] += nx;
+                E[2 * kp + 1] += ny;
+                reached |= (nx & (E[2 * kp] == 0)) | (ny & (E[2 * kp + 1] == 0));
+                lane_neg |= (E[2 * kp] != 0) | (E[2 * kp + 1] != 0);
+                lane_dead &= (E[2 * kp] != 0) & (E[2 * kp + 1] != 0);
+            }
+            if (__any_sync(0xffffffffu, reached)) {
+#pragma unroll
+                for (int kp = 0; kp < KP; ++kp) {
+                    if (E[2 * kp] == 0 && wc2[kp].x == 0.f && ws2[kp].x == 0.f) {
+                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp) * 32 + lane, m);
+                        wc2[kp].x = rw.x;
+                        ws2[kp].x = rw.y;
+                    }
+                    if (E[2 * kp + 1] == 0 && wc2[kp].y == 0.f && ws2[kp].y == 0.f) {
+                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp + 1) * 32 + lane, m);
+                        wc2[kp].y = rw.x;
+                        ws2[kp].y = rw.y;
+                    }
+                }
+            }
+            any_neg = __any_sync(0xffffffffu, lane_neg);
+            all_dead = __all_sync(0xffffffffu, lane_dead);
+        }
+        if (!skip) {
+            __syncwarp();
+            const int row = lane & 15, half = lane >> 4;
+            float sr, si;
+            TraitsF32::row_sum16(xb + row * XS + half * 16, sr, si);
+            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
+            si += __shfl_xor_sync(0xffffffffu, si, 16);
+            const int q = bk * 16 + row;
+            if (half == 0 && q < len) {
+                if constexpr (GACC) {
+                    gacc_add(acc + q, sr, si);
+                } else {
+                    float2 a = acc[q];
+                    a.x += sr;
+                    a.y += si;
+                    acc[q] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return nskip;
+}
+
+// ---------------------------------------------------------------------
+// FP32 column near a pole: every point of the tile has x >= pole_x (sgn = 1)
+// or every point has x <= -pole_x (sgn = -1), and m < pole_mmax.  Near
+// x = +-1 the three-term recurrence has a double root and FP32 rounding of its
+// coefficients and of x sigma grows like l^1.5 eps (1e-3 of lambda_max by
+// l = 2048 at theta ~ 1e-3, mostly at low m).  Here the unfolded recurrence
+// runs in Reinsch's difference form on |x| in the smooth normalisation of the
+// near-pole table (per step and pair: c = a u + e, d = c y + d, y = y + d;
+// u = |x| - 1; tables in build_tables):
+//   y_q = lambda_l(|x|) / gamma~_l  (q = l - m),  d_q = y_q - y_{q-1},
+// gamma~_l = gamma_l (q even), rho gamma_l (q odd).  lambda_l(x) =
+// sgn^q lambda_l(|x|) (mirror symmetry), and the sign-folded accumulators of
+// column_f32x2 hold sigma_q = s_q lambda_l / gamma_l with s_q =
+// (-1)^floor(q/2): the factor s_q sgn^q (q odd ? rho : 1) depends on
+// q mod 4 = j mod 4, sgn and m only, so it is applied to the warp's row
+// value of step j.
+// ---------------------------------------------------------------------
+template <int K, bool GACC = false>
+__device__ __forceinline__ int column_f32x2_pole(const uint32_t* tile, int P, int m, int L,
+                                                  const float4* __restrict__ ae, float sgn, float rho, float lch,
+                                                  float lcl, float2* acc, float2* xb, int lane) {
+    constexpr int KP = K / 2;
+    constexpr int XS = TraitsF32::XSTRIDE;
+    const int len = L - m + 1;
+    float2 u2[KP], y2[KP], d2[KP], wc2[KP], ws2[KP];
+    int E[K];
+    bool lane_neg = false, lane_dead = true;
+#pragma unroll
+    for (int kp = 0; kp < KP; ++kp) {
+        float xv[2], mant[2], cs[2], sn[2], w[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * kp + h;
+            TraitsF32::setup(tile, P, k * 32 + lane, m, lch, lcl, xv[h], mant[h], E[k], cs[h], sn[h], w[h]);
+            lane_neg |= E[k] != 0;
+            lane_dead &= E[k] != 0;
+        }
+        u2[kp] = make_float2(fabsf(xv[0]) - 1.f, fabsf(xv[1]) - 1.f);
+        y2[kp] = make_float2(0.f, 0.f);          // y_{-1}
+        d2[kp] = make_float2(mant[0], mant[1]);  // d_{-1}: the first step gives y_0 = mant
+        wc2[kp] = make_float2(E[2 * kp] == 0 ? w[0] * cs[0] : 0.f, E[2 * kp + 1] == 0 ? w[1] * cs[1] : 0.f);
+        ws2[kp] = make_float2(E[2 * kp] == 0 ? -w[0] * sn[0] : 0.f, E[2 * kp + 1] == 0 ? -w[1] * sn[1] : 0.f);
+    }
+    bool any_neg = __any_sync(0xffffffffu, lane_neg);
+    bool all_dead = __all_sync(0xffffffffu, lane_dead);
+    // row factor of step j: s_q sgn^q (q odd ? rho : 1), q = j (mod 4)
+    const float fr = sgn * rho;
+    const float sj[4] = {1.f, fr, -1.f, -fr};
+
+    int nskip = 0;  // blocks of 16 steps whose accumulation was skipped
+    const int nblk = (len + 15) >> 4;
+    for (int bk = 0; bk < nblk; ++bk) {
+        const bool skip = all_dead;
+        nskip += skip;
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) {
+            float4 cv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cv[c] = __ldg(ae + 16 * bk + 4 * j4 + c);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int j = 4 * j4 + jj;
+                const float2 a2 = make_float2(cv[jj].x, cv[jj].y), e2 = make_float2(cv[jj].z, cv[jj].w);
+#pragma unroll
+                for (int kp = 0; kp < KP; ++kp) {
+                    const float2 c = f2_fma(a2, u2[kp], e2);
+                    d2[kp] = f2_fma(c, y2[kp], d2[kp]);
+                    y2[kp] = f2_add(y2[kp], d2[kp]);
+                }
+                if (!skip) {
+                    float2 r0 = f2_mul(y2[0], wc2[0]), i0 = f2_mul(y2[0], ws2[0]);
+#pragma unroll
+                    for (int kp = 1; kp < KP; ++kp) {
+                        r0 = f2_fma(y2[kp], wc2[kp], r0);
+                        i0 = f2_fma(y2[kp], ws2[kp], i0);
+                    }
+                    xb[j * XS + lane] = make_float2(sj[jj] * (r0.x + r0.y), sj[jj] * (i0.x + i0.y));
+                }
+            }
+        }
+        if (any_neg) {
+            // rescale check once per 16 steps (as column_f32x2, on (y, d))
+            bool reached = false;
+            lane_neg = false;
+            lane_dead = true;
+#pragma unroll
+            for (int kp = 0; kp < KP; ++kp) {
+                const bool nx = needs_rescale(E[2 * kp], y2[kp].x, d2[kp].x);
+                const bool ny = needs_rescale(E[2 * kp + 1], y2[kp].y, d2[kp].y);
+                const float2 f = make_float2(nx ? 0x1p-64f : 1.f, ny ? 0x1p-64f : 1.f);
+                y2[kp] = f2_mul(y2[kp], f);
+                d2[kp] = f2_mul(d2[kp], f);
+                E[2 * kp] += nx;
+                E[2 * kp + 1] += ny;
+                reached |= (nx & (E[2 * kp] == 0)) | (ny & (E[2 * kp + 1] == 0));
+                lane_neg |= (E[2 * kp] != 0) | (E[2 * kp + 1] != 0);
+                lane_dead &= (E[2 * kp] != 0) & (E[2 * kp + 1] != 0);
+            }
+            if (__any_sync(0xffffffffu, reached)) {
+#pragma unroll
+                for (int kp = 0; kp < KP; ++kp) {
+                    if (E[2 * kp] == 0 && wc2[kp].x == 0.f && ws2[kp].x == 0.f) {
+                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp) * 32 + lane, m);
+                        wc2[kp].x = rw.x;
+                        ws2[kp].x = rw.y;
+                    }
+                    if (E[2 * kp + 1] == 0 && wc2[kp].y == 0.f && ws2[kp].y == 0.f) {
+                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp + 1) * 32 + lane, m);
+                        wc2[kp].y = rw.x;
+                        ws2[kp].y = rw.y;
+                    }
+                }
+            }
+            any_neg = __any_sync(0xffffffffu, lane_neg);
+            all_dead = __all_sync(0xffffffffu, lane_dead);
+        }
+        if (!skip) {
+            __syncwarp();
+            const int row = lane & 15, half = lane >> 4;
+            float sr, si;
+            TraitsF32::row_sum16(xb + row * XS + half * 16, sr, si);
+            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
+            si += __shfl_xor_sync(0xffffffffu, si, 16);
+            const int q = bk * 16 + row;
+            if (half == 0 && q < len) {
+                if constexpr (GACC) {
+                    gacc_add(acc + q, sr, si);
+                } else {
+                    float2 a = acc[q];
+                    a.x += sr;
+                    a.y += si;
+                    acc[q] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return nskip;
+}
+
+// +1 if every point of the tile has x >= pole_x, -1 if every point has
+// x <= -pole_x, 0 otherwise; points of weight zero (padding among them)
+// contribute nothing and do not count.  The same answer in every warp of the
+// CTA: all warps read the same tile.
+template <int K>
+__device__ __forceinline__ int tile_near_pole(const uint32_t* tile, int P, float pole_x, int lane) {
+    const float* tf = reinterpret_cast<const float*>(tile);
+    bool np = true, sp = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float x = tf[k * 32 + lane];
+        const bool idle = tf[P + k * 32 + lane] == 0.f;
+        np &= idle | (x >= pole_x);
+        sp &= idle | (x <= -pole_x);
+    }
+    return __all_sync(0xffffffffu, np) ? 1 : (__all_sync(0xffffffffu, sp) ? -1 : 0);
 }
 
 // ---------------------------------------------------------------------
@@ -779,6 +1118,27 @@ __device__ __forceinline__ void flush_acc(typename Tr::real2* acc, int lena, int
     __syncwarp();
 }
 
+// flush of a global accumulator row: lane q mod 16 takes entry q of each
+// column (the lane that added to it), adds it to the FP64 slot and clears it
+__device__ __forceinline__ void flush_gacc(float2* acc, int lena, int lenb, int ma, int mb, int L, double* slot,
+                                           bool first, int lane) {
+    if (lane < 16) {
+        for (int c = 0; c < 2; ++c) {
+            const int len = c ? lenb : lena, m = c ? mb : ma;
+            float2* a = acc + (c ? lena : 0);
+            double2* sp = reinterpret_cast<double2*>(slot) + tri_base(m, L) + m;
+            for (int q = lane; q < len; q += 16) {
+                const float2 v = gacc_take(a + q);
+                double2 s = first ? make_double2(0.0, 0.0) : sp[q];
+                s.x += (double)v.x;
+                s.y += (double)v.y;
+                sp[q] = s;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 template <typename Tr>
 __device__ __forceinline__ void log2c_of(const AnalysisParams& p, int m, typename Tr::real& hi,
                                          typename Tr::real& lo);
@@ -796,8 +1156,8 @@ __device__ __forceinline__ void log2c_of<TraitsF64>(const AnalysisParams& p, int
 // ====================================================================
 //                  persistent analysis kernel (a_lm)
 // ====================================================================
-template <typename Tr, int K, int W, bool PACKED = false>
-__global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant__ AnalysisParams p) {
+template <typename Tr, int K, int W, bool PACKED = false, bool GACC = false, int CH = 0, int MINB = 1>
+__global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_constant__ AnalysisParams p) {
     using real = typename Tr::real;
     using real2 = typename Tr::real2;
     constexpr int P = 32 * K;
@@ -814,7 +1174,10 @@ __global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant_
     real2* accb = xbuf + W * 16 * Tr::XSTRIDE;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    real2* my_acc = accb + warp * accw;
+    // GACC (FP32 only): the warp's accumulator row lives in global memory,
+    // one per (CTA, warp) of the persistent grid
+    real2* my_acc = GACC ? reinterpret_cast<real2*>(p.gacc) + ((int64_t)blockIdx.x * W + warp) * accw
+                         : accb + warp * accw;
     real2* my_xb = xbuf + warp * 16 * Tr::XSTRIDE;
 
     if (threadIdx.x == 0) {
@@ -823,6 +1186,21 @@ __global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant_
         fence_mbar_init();
     }
     __syncthreads();
+    if (p.wait_probe && blockIdx.x == 0) {
+        // Test hook for the timeout path: a bounded wait on a barrier that no
+        // copy and no thread ever arrives at gives up, the CTA records
+        // ERR_TIMEOUT and leaves before it takes a work unit or issues a copy
+        // (the other CTAs take every unit).
+        if (threadIdx.x == 0) {
+            uint64_t* probe = reinterpret_cast<uint64_t*>(smem + 32);
+            mbar_init(probe, 1);
+            fence_mbar_init();
+            if (!mbar_wait_bounded(probe, 0, 1u << 10)) atomicOr(p.err, ERR_TIMEOUT);
+        }
+        __syncthreads();
+        return;
+    }
+    uint32_t blk_skip = 0, blk_all = 0;  // 16-step blocks skipped below range / run (PACKED)
     uint32_t parity0 = 0, parity1 = 0;
 
     for (;;) {
@@ -860,11 +1238,20 @@ __global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant_
                 alpha_b = alpha_base<Tr>(p, mb);
             }
         }
-        for (int i = lane; i < lena + lenb; i += 32) {
-            real2 z;
-            z.x = 0;
-            z.y = 0;
-            my_acc[i] = z;
+        if constexpr (GACC) {
+            // entry q of a column belongs to lane q mod 16 (see gacc_add)
+            float2* ga = reinterpret_cast<float2*>(my_acc);
+            if (lane < 16) {
+                for (int q = lane; q < lena; q += 16) gacc_clear(ga + q);
+                for (int q = lane; q < lenb; q += 16) gacc_clear(ga + lena + q);
+            }
+        } else {
+            for (int i = lane; i < lena + lenb; i += 32) {
+                real2 z;
+                z.x = 0;
+                z.y = 0;
+                my_acc[i] = z;
+            }
         }
         __syncwarp();
         bool first_flush = true;
@@ -887,22 +1274,41 @@ __global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant_
             const bool ok = mbar_wait_bounded(&bars[b], par);
             if (b) parity1 ^= 1u; else parity0 ^= 1u;
             if (__syncthreads_or(!ok)) {
+                // give up on this unit: record the timeout, then wait (bounded)
+                // for every copy this CTA still has in flight, on both buffers
                 if (threadIdx.x == 0) {
                     atomicOr(p.err, ERR_TIMEOUT);
-                    if (t + 1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], b ? parity0 : parity1);
+                    mbar_drain(&bars[b], par);
+                    if (t + 1 < ntiles) mbar_drain(&bars[b ^ 1], b ? parity0 : parity1);
                 }
+                __syncthreads();
                 return;
             }
             const uint32_t* tile = reinterpret_cast<const uint32_t*>(tiles + b * TILE_BYTES);
             if (active) {
+                int pole = 0;
+                if constexpr (PACKED) pole = tile_near_pole<K>(tile, P, p.pole_x, lane);
                 // one inlined copy of the column body, run for both orders of the pair
                 for (int c = 0; c < (single ? 1 : 2); ++c) {
                     const int m = c ? mb : ma;
                     if constexpr (sizeof(real) == 4) {
-                        if constexpr (PACKED)
-                            column_f32x2<K>(tile, P, m, L, p.alpha_f2 + p.colstart[m], c ? lcb : lca,
-                                            c ? lclb : lcla, my_acc + (c ? lena : 0), my_xb, lane);
-                        else
+                        if constexpr (PACKED) {
+                            const int nb = (L - m + 16) >> 4;
+                            int sk;
+                            if (pole && m < p.pole_mmax)
+                                sk = column_f32x2_pole<K, GACC>(tile, P, m, L, p.pole_ae + p.colstart[m], (float)pole,
+                                                           p.pole_rho[m], c ? lcb : lca, c ? lclb : lcla,
+                                                           my_acc + (c ? lena : 0), my_xb, lane);
+                            else if constexpr (CH > 0)
+                                sk = column_f32x2v<K, GACC, CH>(tile, P, m, L, p.alpha_f2 + p.colstart[m],
+                                                                c ? lcb : lca, c ? lclb : lcla,
+                                                                my_acc + (c ? lena : 0), my_xb, lane);
+                            else
+                                sk = column_f32x2<K>(tile, P, m, L, p.alpha_f2 + p.colstart[m], c ? lcb : lca,
+                                                     c ? lclb : lcla, my_acc + (c ? lena : 0), my_xb, lane);
+                            blk_skip += (uint32_t)sk;
+                            blk_all += (uint32_t)nb;
+                        } else
                             column_f32s<K>(tile, P, m, L, p.alpha_f + p.colstart[m], c ? lcb : lca, c ? lclb : lcla,
                                            my_acc + (c ? lena : 0), my_xb, lane);
                     } else
@@ -910,12 +1316,19 @@ __global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant_
                                                my_acc + (c ? lena : 0), my_xb, lane);
                 }
                 if (t == ntiles - 1 || (t + 1) % p.flush_tiles == 0) {
-                    flush_acc<Tr>(my_acc, lena, lenb, ma, mb, L, slot, first_flush, lane);
+                    if constexpr (GACC)
+                        flush_gacc(reinterpret_cast<float2*>(my_acc), lena, lenb, ma, mb, L, slot, first_flush, lane);
+                    else
+                        flush_acc<Tr>(my_acc, lena, lenb, ma, mb, L, slot, first_flush, lane);
                     first_flush = false;
                 }
             }
             __syncthreads();
         }
+    }
+    if (p.stats && lane == 0 && blk_all) {
+        atomicAdd(p.stats, (unsigned long long)blk_skip);
+        atomicAdd(p.stats + 1, (unsigned long long)blk_all);
     }
 }
 
@@ -1142,10 +1555,14 @@ __global__ void __launch_bounds__(G * WG * 32, 1) analysis_f32g_kernel(const __g
             const bool ok = mbar_wait_bounded(&bars[b], par);
             if (b) parity1 ^= 1u; else parity0 ^= 1u;
             if (__syncthreads_or(!ok)) {
+                // give up on this unit: record the timeout, then wait (bounded)
+                // for every copy this CTA still has in flight, on both buffers
                 if (threadIdx.x == 0) {
                     atomicOr(p.err, ERR_TIMEOUT);
-                    if (t + 1 < ntiles) mbar_wait_bounded(&bars[b ^ 1], b ? parity0 : parity1);
+                    mbar_drain(&bars[b], par);
+                    if (t + 1 < ntiles) mbar_drain(&bars[b ^ 1], b ? parity0 : parity1);
                 }
+                __syncthreads();
                 return;
             }
             const uint32_t* tile = reinterpret_cast<const uint32_t*>(tiles + b * TILE_BYTES);
@@ -1286,15 +1703,17 @@ size_t analysis_smem_bytes(int lmax) {
            (size_t)W * accw * sizeof(typename Tr::real2);
 }
 
-template <typename Tr, int K, int W, bool PACKED = false>
+template <typename Tr, int K, int W, bool PACKED = false, bool GACC = false, int CH = 0, int MINB = 1>
 cudaError_t launch_analysis_t(const AnalysisParams& ap, int sm_count, cudaStream_t st, int* grid_out) {
-    const size_t smem = analysis_smem_bytes<Tr, K, W>(ap.lmax);
-    auto kern = analysis_kernel<Tr, K, W, PACKED>;
+    const size_t smem = analysis_smem_bytes<Tr, K, W>(ap.lmax) -
+                        (GACC ? (size_t)W * (((ap.lmax + 2 + 3) & ~3)) * sizeof(typename Tr::real2) : 0);
+    auto kern = analysis_kernel<Tr, K, W, PACKED, GACC, CH, MINB>;
     int occ = 0;
     cudaError_t e = configure_once(kern, W * 32, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * occ;
+    if (GACC && grid > (int64_t)sm_count * ANALYSIS_GACC_CTAS_PER_SM) grid = (int64_t)sm_count * ANALYSIS_GACC_CTAS_PER_SM;
     if (grid > ap.nunits) grid = ap.nunits;
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
@@ -1309,7 +1728,8 @@ cudaError_t launch_analysis_t(const AnalysisParams& ap, int sm_count, cudaStream
 int analysis_tile_points(int prec_is_f64, int k32) {
     if (prec_is_f64) return 32 * 4;
     if (k32 == 108) return 32 * 8 * 4;
-    if (k32 == 116) return 32 * 16;
+    if (k32 == 116 || (k32 >= 118 && k32 <= 122)) return 32 * 16;
+    if (k32 == 124) return 32 * 24;
     return 32 * k32;
 }
 
@@ -1320,6 +1740,11 @@ cudaError_t launch_analysis(const AnalysisParams& ap, int prec_is_f64, int k32, 
         case 8: return launch_analysis_t<TraitsF32, 8, 4>(ap, sm_count, st, grid);
         case 12: return launch_analysis_t<TraitsF32, 12, 4>(ap, sm_count, st, grid);
         case 116: return launch_analysis_t<TraitsF32, 16, 4, true>(ap, sm_count, st, grid);
+        case 118: return launch_analysis_t<TraitsF32, 16, 4, true, true, 1, 3>(ap, sm_count, st, grid);
+        case 119: return launch_analysis_t<TraitsF32, 16, 4, true, false, 1, 1>(ap, sm_count, st, grid);
+        case 120: return launch_analysis_t<TraitsF32, 16, 4, true, false, 2, 1>(ap, sm_count, st, grid);
+        case 122: return launch_analysis_t<TraitsF32, 16, 4, true, true, 2, 3>(ap, sm_count, st, grid);
+        case 124: return launch_analysis_t<TraitsF32, 24, 4, true, true, 2, 2>(ap, sm_count, st, grid);
         case 108: return launch_analysis_f32g<8, 4, 4>(ap, sm_count, st, grid);
         default: return launch_analysis_t<TraitsF32, 16, 4>(ap, sm_count, st, grid);
     }

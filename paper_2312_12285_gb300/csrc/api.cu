@@ -75,6 +75,12 @@ struct pointsht_plan_s {
     void* blob = nullptr;
     float* alpha_f = nullptr;
     float2* alpha_f2 = nullptr;  // (alpha, alpha) pairs for packed f32x2 arithmetic
+    float4* pole_ae = nullptr;   // near-pole tables (a, a, a - 2, a - 2), see build_tables
+    float* pole_rho = nullptr;   // odd-chain scale rho_m of the near-pole normalisation
+    int pole_mmax = 256;         // ... for orders m < pole_mmax
+    float pole_x = 0.9f;         // tiles (warps) whose points all have |x| >= pole_x take the near-pole form
+    int wait_probe = 0;          // test hook of the timeout path (pointsht_plan_set_wait_probe)
+    unsigned long long* stats = nullptr;  // optional skip counters (pointsht_plan_set_skip_counters)
     double* alpha_d = nullptr;
     int64_t* colstart = nullptr;
     double* gamma = nullptr;
@@ -120,8 +126,25 @@ extern "C" const char* pointsht_last_error(void) { return g_last_error.c_str(); 
 // Built in long double on the host: lambda-form recurrence coefficients
 // (App. A divided through by sqrt((2l+1)/4pi)), their gamma rescaling and
 // log2 c_m = log2 |lambda_mm| - m log2 sin(theta).
+// Tables of the sign-folded FP32/FP64 recurrence (see analysis.cu): gamma_l =
+// B_l gamma_{l-2} removes B from the recurrence on each parity chain of
+// q = l - m (gamma_m = gamma_{m+1} = 1), alpha~ its coefficients.
+//
+// Near-pole table.  Near x = +-1 the recurrence mu_l = a_l x mu_{l-1} -
+// mu_{l-2} (mu = lambda / gamma) has a double root at 1, where FP32 rounding
+// of a_l and of x mu grows like l^1.5 eps.  Reinsch's form carries the
+// difference d_l = mu_l - mu_{l-1} instead,
+//   d_l = (a_l u + e_l) mu_{l-1} + d_{l-1},  mu_l = mu_{l-1} + d_l,
+//   u = |x| - 1 (exact in FP32),  e_l = a_l - 2 (stored to full relative precision),
+// so that only small quantities carry coefficient and product rounding.  It
+// needs mu smooth in l, so there the odd chain of gamma is scaled by rho_m,
+// chosen so that it meets the even chain at lmax (geometric mean of the
+// neighbouring even values): a_l then tends to 2 instead of alternating
+// between two constants.  Entry (m, q) of pae: (a_l, a_l, e_l, e_l) for
+// l = m + q, q >= 1 (q = 0 unused); prho[m] = rho_m.
 static void build_tables(int L, std::vector<int64_t>& colstart, std::vector<float>& af, std::vector<double>& ad,
-                         std::vector<double>& gamma, std::vector<double>& l2c) {
+                         std::vector<double>& gamma, std::vector<double>& l2c, std::vector<float4>& pae,
+                         std::vector<float>& prho) {
     colstart.assign(L + 2, 0);
     for (int m = 0; m <= L; ++m) {
         const int64_t len = L - m + 1;
@@ -130,6 +153,8 @@ static void build_tables(int L, std::vector<int64_t>& colstart, std::vector<floa
     const int64_t acol = colstart[L + 1];
     af.assign(acol, 0.f);
     ad.assign(acol, 0.0);
+    pae.assign(acol + 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    prho.assign(L + 1, 1.f);
     const int64_t M = (int64_t)(L + 1) * (L + 2) / 2;
     gamma.assign(M, 0.0);
     l2c.assign(L + 1, 0.0);
@@ -139,28 +164,42 @@ static void build_tables(int L, std::vector<int64_t>& colstart, std::vector<floa
         l2c[m] = (double)(0.5L * log2l((2.0L * m + 1.0L) / (4.0L * 3.141592653589793238462643383279502884L)) +
                           0.5L * sumlog);
         const int64_t base = tri_base(m, L);
-        std::vector<long double> g(L - m + 1, 1.0L);
+        const int n = L - m;
+        std::vector<long double> g(n + 1, 1.0L);
         for (int l = m + 2; l <= L; ++l) {
             const long double ll = l, mm = m;
             const long double B = sqrtl((2 * ll + 1) * ((ll - 1) * (ll - 1) - mm * mm) /
                                         ((2 * ll - 3) * (ll * ll - mm * mm)));
             g[l - m] = B * g[l - m - 2];
         }
+        long double rho = 1.0L;
+        if (n >= 2) {
+            const int qo = (n & 1) ? n : n - 1;  // last odd q
+            const long double target = qo + 1 <= n ? sqrtl(g[qo - 1] * g[qo + 1]) : g[qo - 1];
+            rho = target / g[qo];
+        }
+        prho[m] = (float)rho;
         // sigma_q = s_q mu_q with s_q = (-1)^floor(q/2), q = l - m, turns
-        // mu_l = alpha_l x mu_{l-1} - mu_{l-2} into
-        // sigma_l = (s_q/s_{q-1}) alpha_l x sigma_{l-1} + sigma_{l-2}
+        // mu_l = a_l x mu_{l-1} - mu_{l-2} into
+        // sigma_l = (s_q/s_{q-1}) a_l x sigma_{l-1} + sigma_{l-2}
         // (no negation in the inner loop); s_q is folded into gamma.
         for (int l = m; l <= L; ++l) {
             const long double ll = l, mm = m;
             const int q = l - m;
             const int sq = ((q >> 1) & 1) ? -1 : 1;
             const int sq1 = q >= 1 ? ((((q - 1) >> 1) & 1) ? -1 : 1) : 1;
-            long double a = 0.0L;
-            if (l == m + 1) a = sqrtl(2 * mm + 3);
-            if (l >= m + 2) {
-                const long double A = sqrtl((4 * ll * ll - 1) / (ll * ll - mm * mm));
-                a = A * g[l - m - 1] / g[l - m];
+            long double A = 0.0L;
+            if (l == m + 1) A = sqrtl(2 * mm + 3);
+            if (l >= m + 2) A = sqrtl((4 * ll * ll - 1) / (ll * ll - mm * mm));
+            if (q >= 1) {
+                // smooth normalisation: gamma~_q = gamma_q (q even), rho gamma_q (q odd)
+                const long double gs_prev = ((q - 1) & 1) ? g[q - 1] * rho : g[q - 1];
+                const long double gs = (q & 1) ? g[q] * rho : g[q];
+                const long double as = A * gs_prev / gs;
+                const float pa = (float)as, pe = (float)(as - 2.0L);
+                pae[colstart[m] + q] = make_float4(pa, pa, pe, pe);
             }
+            long double a = q >= 1 ? A * g[q - 1] / g[q] : 0.0L;
             a *= (long double)(sq * sq1);
             af[colstart[m] + q] = (float)a;
             ad[colstart[m] + q] = (double)a;
@@ -188,7 +227,9 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     std::vector<int64_t> colstart;
     std::vector<float> af;
     std::vector<double> ad, gamma, l2c;
-    build_tables(lmax, colstart, af, ad, gamma, l2c);
+    std::vector<float4> pae;
+    std::vector<float> prho;
+    build_tables(lmax, colstart, af, ad, gamma, l2c, pae, prho);
     std::vector<float> lh(lmax + 1), ll(lmax + 1);
     for (int m = 0; m <= lmax; ++m) {
         lh[m] = (float)l2c[m];
@@ -201,7 +242,8 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     const size_t s_af2 = up(af2.size() * 8);
     const size_t s_af = up(af.size() * 4), s_ad = up(ad.size() * 8), s_cs = up(colstart.size() * 8),
                  s_g = up(gamma.size() * 8), s_lh = up(lh.size() * 4), s_l2 = up(l2c.size() * 8), s_err = 256;
-    const size_t total = s_af + s_af2 + s_ad + s_cs + s_g + 2 * s_lh + s_l2 + s_err;
+    const size_t s_pae = up(pae.size() * 16), s_rho = up(prho.size() * 4);
+    const size_t total = s_af + s_af2 + s_ad + s_cs + s_g + 2 * s_lh + s_l2 + s_err + s_pae + s_rho;
     pointsht_plan p = new pointsht_plan_s();
     p->lmax = lmax;
     p->device = dev;
@@ -231,6 +273,10 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     p->log2c = reinterpret_cast<double*>(b);
     b += s_l2;
     p->err = reinterpret_cast<unsigned*>(b);
+    b += s_err;
+    p->pole_ae = reinterpret_cast<float4*>(b);
+    b += s_pae;
+    p->pole_rho = reinterpret_cast<float*>(b);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(p->alpha_f, af.data(), af.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->alpha_f2, af2.data(), af2.size() * 8, cudaMemcpyHostToDevice);
@@ -241,6 +287,8 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     if (e == cudaSuccess) e = cudaMemcpy(p->log2c_lo, ll.data(), ll.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->log2c, l2c.data(), l2c.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, s_err);
+    if (e == cudaSuccess) e = cudaMemcpy(p->pole_ae, pae.data(), pae.size() * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->pole_rho, prho.data(), prho.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(p->blob);
         delete p;
@@ -274,12 +322,33 @@ extern "C" pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, v
 
 extern "C" pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, int32_t chunk_log2) {
     if (!plan) return fail(POINTSHT_EINVAL, "set_tuning: plan is NULL");
-    if (!(variant == 0 || variant == 8 || variant == 12 || variant == 16 || variant == 108 || variant == 116))
+    if (!(variant == 0 || variant == 8 || variant == 12 || variant == 16 || variant == 108 || variant == 116 ||
+          variant == 118 || variant == 119 || variant == 120 || variant == 122 || variant == 124))
         return fail(POINTSHT_EINVAL, "set_tuning: unknown variant %d", variant);
     if (!(chunk_log2 == 0 || (chunk_log2 >= 10 && chunk_log2 <= 22)))
         return fail(POINTSHT_EINVAL, "set_tuning: chunk_log2 %d outside {0} or [10, 22]", chunk_log2);
     plan->variant = variant;
     plan->chunk_log2 = chunk_log2;
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_plan_set_pole_threshold(pointsht_plan plan, float pole_x) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_pole_threshold: plan is NULL");
+    if (!(pole_x >= 0.5f)) return fail(POINTSHT_EINVAL, "set_pole_threshold: %g is below 0.5 (or NaN)", pole_x);
+    plan->pole_x = pole_x;
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_plan_set_skip_counters(pointsht_plan plan, void* counters) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_skip_counters: plan is NULL");
+    if ((uintptr_t)counters % 8) return fail(POINTSHT_EINVAL, "set_skip_counters: counters not 8-byte aligned");
+    plan->stats = static_cast<unsigned long long*>(counters);
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_plan_set_wait_probe(pointsht_plan plan, int32_t enable) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_wait_probe: plan is NULL");
+    plan->wait_probe = enable ? 1 : 0;
     return POINTSHT_OK;
 }
 
@@ -313,7 +382,7 @@ struct Layout {
     int32_t slot0[PSHT_MAX_FIELDS] = {};
     int64_t unit0[PSHT_MAX_FIELDS] = {};
     // byte offsets in the workspace
-    size_t pts_off = 0, slots_off = 0, counter_off = 0, hist_off = 0, fwd_end = 0;
+    size_t pts_off = 0, slots_off = 0, counter_off = 0, hist_off = 0, gacc_off = 0, fwd_end = 0;
     int64_t nranges = 0;
     size_t gtab_off = 0, bwd_end = 0, shot_off = 0, total = 0;
 };
@@ -354,7 +423,7 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     lo.k32 = 116;
     if (const char* e = getenv("POINTSHT_K")) {
         const int k = atoi(e);
-        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116) lo.k32 = k;
+        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116 || (k >= 118 && k <= 124)) lo.k32 = k;
     }
     if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
@@ -410,6 +479,10 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     for (int c = 0; c < ncat; ++c) lo.nranges += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
     lo.hist_off = b;
     b += up256((size_t)std::max<int64_t>(lo.nranges, 1) * SORT_BUCKETS * 8);
+    if (!is_f64 && (lo.k32 == 118 || lo.k32 == 122 || lo.k32 == 124)) {  // rows of every resident (CTA, warp)
+        lo.gacc_off = b;
+        b += up256((size_t)plan->sm_count * ANALYSIS_GACC_CTAS_PER_SM * WARPS * ((L + 2 + 3) & ~3) * 8);
+    }
     lo.fwd_end = b;
     if (is_f64) {  // catalog-order adjoint: the table alone
         lo.gtab_off = 0;
@@ -542,7 +615,14 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
         ap.log2c_hi = plan->log2c_hi;
         ap.log2c_lo = plan->log2c_lo;
         ap.log2c = plan->log2c;
+        ap.pole_ae = plan->pole_ae;
+        ap.pole_x = plan->pole_x;
+        ap.pole_rho = plan->pole_rho;
+        ap.pole_mmax = plan->pole_mmax;
+        ap.wait_probe = plan->wait_probe;
+        ap.stats = plan->stats;
         ap.slots = reinterpret_cast<double*>(ws + lo.slots_off);
+        ap.gacc = lo.gacc_off ? reinterpret_cast<float2*>(ws + lo.gacc_off) : nullptr;
         ap.counter = reinterpret_cast<int*>(ws + lo.counter_off);
         ap.err = plan->err;
         if (plan->ev_start) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
@@ -1094,6 +1174,10 @@ static pointsht_status run_adjoint(pointsht_plan plan, const pointsht_catalog* c
         ap.ntot = lo.ntot;
         for (int f = 0; f < nfield; ++f) ap.fld[f].off = lo.off[f];
         ap.alpha2 = plan->alpha_f2;
+        ap.pole_ae = plan->pole_ae;
+        ap.pole_x = plan->pole_x;
+        ap.pole_rho = plan->pole_rho;
+        ap.pole_mmax = plan->pole_mmax;
         e = launch_adjoint_sorted(ap, grad_alm, plan->gamma, synth, st);
         if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "%s: adjoint: %s", who, cudaGetErrorString(e));
         return POINTSHT_OK;

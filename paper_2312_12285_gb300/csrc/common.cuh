@@ -22,6 +22,7 @@
 #include <utility>
 
 #define PSHT_MAX_FIELDS 64
+#define ANALYSIS_GACC_CTAS_PER_SM 4   // accumulator rows the workspace holds per SM (variant 118)
 #define PSHT_MAX_CATS 128
 
 namespace psht {
@@ -108,7 +109,14 @@ struct AnalysisParams {
     const float* log2c_hi;  // log2 c_m as float pair
     const float* log2c_lo;
     const double* log2c;    // log2 c_m in FP64
+    const float4* pole_ae;  // near-pole form: (a, a, a - 2, a - 2) per (m, q), padded columns
+    float pole_x;           // a tile whose points all have |x| >= pole_x takes the near-pole form
+    const float* pole_rho;  // near-pole form: odd-chain scale per m
+    int32_t pole_mmax;      // ... for orders m < pole_mmax
+    int32_t wait_probe;     // test hook: CTA 0 waits on a barrier nothing arrives at, then leaves
     double* slots;          // [slot][nmodes][2]
+    float2* gacc;           // variant 118: accumulator rows [CTA][warp][(lmax + 2 + 3) & ~3]
+    unsigned long long* stats;  // optional: [0] += 16-step blocks whose accumulation was skipped, [1] += all
     int* counter;
     unsigned* err;
 #ifdef __CUDACC__
@@ -138,15 +146,20 @@ struct PrepParams {
     unsigned* err;
 };
 
-#define SORT_BUCKETS 256
+#define SORT_XBINS 256          // bins of |x| in [0, 1]
+#define SORT_SPLIT 224          // from |x| >= 224/256 on, x < 0 and x > 0 get separate buckets
+#define SORT_BUCKETS (SORT_XBINS + SORT_XBINS - SORT_SPLIT)
 #define SORT_RANGE 4096  // points per CTA range of the counting sort
 
 #ifdef __CUDACC__
-// |x| bucket of the counting sort (points ordered by |x|, see analysis.cu)
+// Bucket of the counting sort: points are ordered by |x| (see analysis.cu);
+// near the poles the two signs of x are kept apart, so that a tile of points
+// near a pole lies on one side (the near-pole form mirrors x < 0 onto |x|).
 __device__ __forceinline__ int x_bucket(double x) {
     const double a = fabs(x);
-    int b = (int)(a * SORT_BUCKETS);
-    return b < 0 ? 0 : (b >= SORT_BUCKETS ? SORT_BUCKETS - 1 : b);
+    int b = (int)(a * SORT_XBINS);
+    b = b < 0 ? 0 : (b >= SORT_XBINS ? SORT_XBINS - 1 : b);
+    return (b >= SORT_SPLIT && x < 0.0) ? b + SORT_XBINS - SORT_SPLIT : b;
 }
 
 // phi (radians, any finite value) as a 64-bit fixed-point fraction of a turn
@@ -262,6 +275,10 @@ struct AdjointParams {
     int64_t ntot;
     FieldDesc fld[PSHT_MAX_FIELDS];
     const float2* alpha2;
+    const float4* pole_ae;   // near-pole form (see the analysis)
+    const float* pole_rho;
+    float pole_x;
+    int32_t pole_mmax;
 };
 
 __host__ __device__ inline int64_t tri_base(int64_t m, int64_t lmax) {
@@ -313,6 +330,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// After a bounded wait gave up: wait once more, bounded but far longer, for
+// the copy still owed to `bar` (the phase of parity `parity`), so that no bulk
+// copy lands in the shared memory of a CTA that has exited.  Called by the one
+// thread that issues the copies, before the CTA returns.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+    return mbar_wait_bounded(bar, parity, 1u << 26);
 }
 
 // -------------------------------------------- float-pair arithmetic --

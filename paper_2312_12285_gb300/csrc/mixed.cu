@@ -308,7 +308,12 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
             const bool ok = mbar_wait_bounded(bar, parity);
             parity ^= 1u;
             if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicOr(p.err, ERR_TIMEOUT);
+                // record the timeout and wait (bounded) for the copy in flight
+                if (threadIdx.x == 0) {
+                    atomicOr(p.err, ERR_TIMEOUT);
+                    mbar_drain(bar, parity ^ 1u);
+                }
+                __syncthreads();
                 return;
             }
             const float* tf = reinterpret_cast<const float*>(tile);

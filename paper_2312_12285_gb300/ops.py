@@ -9,6 +9,7 @@ marshal pointers.  Complex gradients follow torch's convention
 from __future__ import annotations
 
 import ctypes
+import math
 import threading
 from dataclasses import dataclass
 
@@ -64,6 +65,22 @@ class Plan:
         """FP32 analysis kernel variant and accumulation chunk size (0 = defaults)."""
         _lib.check(self.lib.pointsht_plan_set_tuning(self.handle, int(variant), int(chunk_log2)), "set_tuning")
         self.tuning = (int(variant), int(chunk_log2))
+
+    def set_pole_threshold(self, pole_x: float):
+        """Tiles of points all with |x| >= pole_x (one sign) run the near-pole
+        form of the FP32 recurrence; above 1 turns it off."""
+        _lib.check(self.lib.pointsht_plan_set_pole_threshold(self.handle, float(pole_x)), "set_pole_threshold")
+
+    def set_skip_counters(self, counters=None):
+        """counters: a zeroed int64 CUDA tensor of 2 entries (or None to turn
+        off); FP32 analysis launches add skipped / all 16-step blocks."""
+        ptr = None if counters is None else ctypes.c_void_p(counters.data_ptr())
+        _lib.check(self.lib.pointsht_plan_set_skip_counters(self.handle, ptr), "set_skip_counters")
+
+    def set_wait_probe(self, enable: bool):
+        """Test hook: the first CTA of each analysis launch gives up a bounded
+        wait on a barrier nothing arrives at (see pointsht.h)."""
+        _lib.check(self.lib.pointsht_plan_set_wait_probe(self.handle, int(bool(enable))), "set_wait_probe")
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -188,6 +205,19 @@ def workspace_bytes_interp(plan: Plan, cats, nfield: int, ntheta: int) -> int:
 def default_ntheta(lmax: int) -> int:
     """16 samples per multipole (relative interpolation error ~1.5e-6), at most 32768."""
     return min(32768, 16 * lmax)
+
+
+def ntheta_for_tolerance(lmax: int, cl_tol: float = 1e-4, safety: float = 4.0) -> int:
+    """Samples in theta for a pseudo-C_l error budget, from the cubic Hermite
+    spline's h^4 error (App. "Interpolation"): the C_l error measured at 16
+    samples per multipole is ~4.3e-6 (lmax 2048, lognormal workload), so
+    err(N) ~ 4.3e-6 (16 lmax / N)^4; N is the smallest even count with
+    err(N) <= cl_tol / safety (10 lmax for the default 1e-4 / 4), at most
+    32768."""
+    ratio = (cl_tol / safety / 4.3e-6) ** 0.25
+    n = int(math.ceil(16.0 * lmax / max(ratio, 1.0)))
+    n += n & 1
+    return max(2, min(32768, n))
 
 
 def alm_interp(plan: Plan, cats, nfield: int = 1, ntheta=None, out=None, workspace=None, stream=None):
