@@ -133,9 +133,8 @@ pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, void* start,
 /* Tuning of the FP32 analysis kernel for this plan (the paper has no
  * counterpart; chosen by the autotuner): variant 0 = library default, or
  * 8 / 12 / 16 = points per lane with scalar FMAs, 116 = 16 points per lane as
- * f32x2 pairs, 118 = 116 with the accumulator rows in global memory (three
- * CTAs per SM), 108 = four warps sharing each order pair's accumulator (only
- * 116 and 118 carry the near-pole form, pointsht_plan_set_pole_threshold);
+ * f32x2 pairs, 108 = four warps sharing each order pair's accumulator (only
+ * 116 carries the near-pole form, pointsht_plan_set_pole_threshold);
  * chunk_log2 0 = automatic, else log2 of the points per accumulation chunk
  * (10..22).  Changes the workspace size: query pointsht_workspace_size after
  * setting.  EINVAL for values outside these sets. */
@@ -154,7 +153,7 @@ pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, in
 pointsht_status pointsht_plan_set_pole_threshold(pointsht_plan plan, float pole_x);
 
 /* Measurement hook (the paper has no counterpart): while counters is not
- * NULL, every FP32 analysis launch of variant 116 / 118 adds to the device
+ * NULL, every FP32 analysis launch of variant 116 adds to the device
  * array counters[2] (uint64, caller-owned, zeroed by the caller) the number of
  * 16-step recurrence blocks (times the warp's points) whose accumulation was
  * skipped because every point of the warp was still below the FP32 range

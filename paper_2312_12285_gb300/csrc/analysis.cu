@@ -490,23 +490,6 @@ __device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
     return d;
 }
 
-// Per-warp FP32 accumulator rows in global memory (variant 118).  Entry q of
-// a column is updated only by lane q mod 16 of the warp that owns the row, by
-// a fire-and-forget atomic add at device scope (performed in L2, in that
-// lane's program order, so the sum is the same bit for bit on every run); the
-// same lane reads and clears it with device-scope loads and stores, which are
-// ordered after its own adds.
-__device__ __forceinline__ void gacc_add(float2* p, float a, float b) { atomicAdd(p, make_float2(a, b)); }
-__device__ __forceinline__ float2 gacc_take(float2* p) {
-    float2 v;
-    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
-    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(0.f), "f"(0.f) : "memory");
-    return v;
-}
-__device__ __forceinline__ void gacc_clear(float2* p) {
-    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(0.f), "f"(0.f) : "memory");
-}
-
 __device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
     float2 d;
     asm("add.rn.f32x2 %0, %1, %2;"
@@ -671,158 +654,6 @@ __device__ __forceinline__ int column_f32x2(const uint32_t* tile, int P, int m, 
 
 
 // ---------------------------------------------------------------------
-// FP32 column, variants 118-124: the arithmetic of column_f32x2, with the
-// coefficients fetched four steps at a time (one group ahead) instead of a
-// whole block ahead (fewer registers), the accumulator row in shared memory
-// or in global memory (GACC: gacc_add; a CTA then needs far less shared
-// memory), and the accumulation over the lane's pairs in CH = 1 or 2 chains
-// per component (two halve the dependency chain, for one packed add more).
-// ---------------------------------------------------------------------
-template <int K, bool GACC, int CH>
-__device__ __forceinline__ int column_f32x2v(const uint32_t* tile, int P, int m, int L,
-                                               const float2* __restrict__ alpha2, float lch, float lcl, float2* acc,
-                                               float2* xb, int lane) {
-    constexpr int KP = K / 2;
-    constexpr int XS = TraitsF32::XSTRIDE;
-    const int len = L - m + 1;
-    float2 x2[KP], p1[KP], p2[KP], wc2[KP], ws2[KP];
-    int E[K];
-    bool lane_neg = false, lane_dead = true;
-#pragma unroll
-    for (int kp = 0; kp < KP; ++kp) {
-        float xv[2], mant[2], cs[2], sn[2], w[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = 2 * kp + h;
-            TraitsF32::setup(tile, P, k * 32 + lane, m, lch, lcl, xv[h], mant[h], E[k], cs[h], sn[h], w[h]);
-            lane_neg |= E[k] != 0;
-            lane_dead &= E[k] != 0;
-        }
-        x2[kp] = make_float2(xv[0], xv[1]);
-        p1[kp] = make_float2(0.f, 0.f);          // sigma_{m-1}
-        p2[kp] = make_float2(mant[0], mant[1]);  // sigma_{m-2}
-        wc2[kp] = make_float2(E[2 * kp] == 0 ? w[0] * cs[0] : 0.f, E[2 * kp + 1] == 0 ? w[1] * cs[1] : 0.f);
-        ws2[kp] = make_float2(E[2 * kp] == 0 ? -w[0] * sn[0] : 0.f, E[2 * kp + 1] == 0 ? -w[1] * sn[1] : 0.f);
-    }
-    bool any_neg = __any_sync(0xffffffffu, lane_neg);
-    bool all_dead = __all_sync(0xffffffffu, lane_dead);
-
-    int nskip = 0;  // blocks of 16 steps whose accumulation was skipped
-    const int nblk = (len + 15) >> 4;
-    // float4 i holds the pairs (alpha_{2i}, alpha_{2i}), (alpha_{2i+1}, alpha_{2i+1});
-    // a group of four steps is two of them.  The group after the column's last
-    // lies in the next column or in the 32 zero entries after the last one.
-    const float4* a4 = reinterpret_cast<const float4*>(alpha2);
-    float4 n0 = __ldg(a4), n1 = __ldg(a4 + 1);
-    for (int bk = 0; bk < nblk; ++bk) {
-        const bool skip = all_dead;
-        nskip += skip;  // decided for this whole block of 16 steps
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const float2 av[4] = {make_float2(n0.x, n0.y), make_float2(n0.z, n0.w), make_float2(n1.x, n1.y),
-                                  make_float2(n1.z, n1.w)};
-            n0 = __ldg(a4 + 8 * bk + 2 * g + 2);
-            n1 = __ldg(a4 + 8 * bk + 2 * g + 3);
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int j = 4 * g + jj;
-                float2 t[KP];
-#pragma unroll
-                for (int kp = 0; kp < KP; ++kp) t[kp] = f2_mul(x2[kp], p1[kp]);
-#pragma unroll
-                for (int kp = 0; kp < KP; ++kp) {
-                    const float2 sg = f2_fma(av[jj], t[kp], p2[kp]);
-                    p2[kp] = p1[kp];
-                    p1[kp] = sg;
-                }
-                if (!skip) {
-                    if constexpr (CH == 1) {
-                        float2 r0 = f2_mul(p1[0], wc2[0]), i0 = f2_mul(p1[0], ws2[0]);
-#pragma unroll
-                        for (int kp = 1; kp < KP; ++kp) {
-                            r0 = f2_fma(p1[kp], wc2[kp], r0);
-                            i0 = f2_fma(p1[kp], ws2[kp], i0);
-                        }
-                        xb[j * XS + lane] = make_float2(r0.x + r0.y, i0.x + i0.y);
-                    } else {
-                        constexpr int H = KP / 2;
-                        float2 r0 = f2_mul(p1[0], wc2[0]), i0 = f2_mul(p1[0], ws2[0]);
-                        float2 r1 = f2_mul(p1[H], wc2[H]), i1 = f2_mul(p1[H], ws2[H]);
-#pragma unroll
-                        for (int kp = 1; kp < H; ++kp) {
-                            r0 = f2_fma(p1[kp], wc2[kp], r0);
-                            i0 = f2_fma(p1[kp], ws2[kp], i0);
-                            r1 = f2_fma(p1[H + kp], wc2[H + kp], r1);
-                            i1 = f2_fma(p1[H + kp], ws2[H + kp], i1);
-                        }
-                        r0 = f2_add(r0, r1);
-                        i0 = f2_add(i0, i1);
-                        xb[j * XS + lane] = make_float2(r0.x + r0.y, i0.x + i0.y);
-                    }
-                }
-            }
-        }
-        if (any_neg) {
-            // rescale check once per 16 steps (as column_f32x2)
-            bool reached = false;
-            lane_neg = false;
-            lane_dead = true;
-#pragma unroll
-            for (int kp = 0; kp < KP; ++kp) {
-                const bool nx = needs_rescale(E[2 * kp], p1[kp].x, p2[kp].x);
-                const bool ny = needs_rescale(E[2 * kp + 1], p1[kp].y, p2[kp].y);
-                const float2 f = make_float2(nx ? 0x1p-64f : 1.f, ny ? 0x1p-64f : 1.f);
-                p1[kp] = f2_mul(p1[kp], f);
-                p2[kp] = f2_mul(p2[kp], f);
-                E[2 * kp] += nx;
-                E[2 * kp + 1] += ny;
-                reached |= (nx & (E[2 * kp] == 0)) | (ny & (E[2 * kp + 1] == 0));
-                lane_neg |= (E[2 * kp] != 0) | (E[2 * kp + 1] != 0);
-                lane_dead &= (E[2 * kp] != 0) & (E[2 * kp + 1] != 0);
-            }
-            if (__any_sync(0xffffffffu, reached)) {
-#pragma unroll
-                for (int kp = 0; kp < KP; ++kp) {
-                    if (E[2 * kp] == 0 && wc2[kp].x == 0.f && ws2[kp].x == 0.f) {
-                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp) * 32 + lane, m);
-                        wc2[kp].x = rw.x;
-                        ws2[kp].x = rw.y;
-                    }
-                    if (E[2 * kp + 1] == 0 && wc2[kp].y == 0.f && ws2[kp].y == 0.f) {
-                        const float2 rw = restore_weight<TraitsF32>(tile, P, (2 * kp + 1) * 32 + lane, m);
-                        wc2[kp].y = rw.x;
-                        ws2[kp].y = rw.y;
-                    }
-                }
-            }
-            any_neg = __any_sync(0xffffffffu, lane_neg);
-            all_dead = __all_sync(0xffffffffu, lane_dead);
-        }
-        if (!skip) {
-            __syncwarp();
-            const int row = lane & 15, half = lane >> 4;
-            float sr, si;
-            TraitsF32::row_sum16(xb + row * XS + half * 16, sr, si);
-            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
-            si += __shfl_xor_sync(0xffffffffu, si, 16);
-            const int q = bk * 16 + row;
-            if (half == 0 && q < len) {
-                if constexpr (GACC) {
-                    gacc_add(acc + q, sr, si);
-                } else {
-                    float2 a = acc[q];
-                    a.x += sr;
-                    a.y += si;
-                    acc[q] = a;
-                }
-            }
-            __syncwarp();
-        }
-    }
-    return nskip;
-}
-
-// ---------------------------------------------------------------------
 // FP32 column near a pole: every point of the tile has x >= pole_x (sgn = 1)
 // or every point has x <= -pole_x (sgn = -1), and m < pole_mmax.  Near
 // x = +-1 the three-term recurrence has a double root and FP32 rounding of its
@@ -839,7 +670,7 @@ __device__ __forceinline__ int column_f32x2v(const uint32_t* tile, int P, int m,
 // q mod 4 = j mod 4, sgn and m only, so it is applied to the warp's row
 // value of step j.
 // ---------------------------------------------------------------------
-template <int K, bool GACC = false>
+template <int K>
 __device__ __forceinline__ int column_f32x2_pole(const uint32_t* tile, int P, int m, int L,
                                                   const float4* __restrict__ ae, float sgn, float rho, float lch,
                                                   float lcl, float2* acc, float2* xb, int lane) {
@@ -947,14 +778,10 @@ __device__ __forceinline__ int column_f32x2_pole(const uint32_t* tile, int P, in
             si += __shfl_xor_sync(0xffffffffu, si, 16);
             const int q = bk * 16 + row;
             if (half == 0 && q < len) {
-                if constexpr (GACC) {
-                    gacc_add(acc + q, sr, si);
-                } else {
-                    float2 a = acc[q];
-                    a.x += sr;
-                    a.y += si;
-                    acc[q] = a;
-                }
+                float2 a = acc[q];
+                a.x += sr;
+                a.y += si;
+                acc[q] = a;
             }
             __syncwarp();
         }
@@ -1118,27 +945,6 @@ __device__ __forceinline__ void flush_acc(typename Tr::real2* acc, int lena, int
     __syncwarp();
 }
 
-// flush of a global accumulator row: lane q mod 16 takes entry q of each
-// column (the lane that added to it), adds it to the FP64 slot and clears it
-__device__ __forceinline__ void flush_gacc(float2* acc, int lena, int lenb, int ma, int mb, int L, double* slot,
-                                           bool first, int lane) {
-    if (lane < 16) {
-        for (int c = 0; c < 2; ++c) {
-            const int len = c ? lenb : lena, m = c ? mb : ma;
-            float2* a = acc + (c ? lena : 0);
-            double2* sp = reinterpret_cast<double2*>(slot) + tri_base(m, L) + m;
-            for (int q = lane; q < len; q += 16) {
-                const float2 v = gacc_take(a + q);
-                double2 s = first ? make_double2(0.0, 0.0) : sp[q];
-                s.x += (double)v.x;
-                s.y += (double)v.y;
-                sp[q] = s;
-            }
-        }
-    }
-    __syncwarp();
-}
-
 template <typename Tr>
 __device__ __forceinline__ void log2c_of(const AnalysisParams& p, int m, typename Tr::real& hi,
                                          typename Tr::real& lo);
@@ -1156,8 +962,8 @@ __device__ __forceinline__ void log2c_of<TraitsF64>(const AnalysisParams& p, int
 // ====================================================================
 //                  persistent analysis kernel (a_lm)
 // ====================================================================
-template <typename Tr, int K, int W, bool PACKED = false, bool GACC = false, int CH = 0, int MINB = 1>
-__global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_constant__ AnalysisParams p) {
+template <typename Tr, int K, int W, bool PACKED = false>
+__global__ void __launch_bounds__(W * 32) analysis_kernel(const __grid_constant__ AnalysisParams p) {
     using real = typename Tr::real;
     using real2 = typename Tr::real2;
     constexpr int P = 32 * K;
@@ -1174,10 +980,7 @@ __global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_con
     real2* accb = xbuf + W * 16 * Tr::XSTRIDE;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // GACC (FP32 only): the warp's accumulator row lives in global memory,
-    // one per (CTA, warp) of the persistent grid
-    real2* my_acc = GACC ? reinterpret_cast<real2*>(p.gacc) + ((int64_t)blockIdx.x * W + warp) * accw
-                         : accb + warp * accw;
+    real2* my_acc = accb + warp * accw;
     real2* my_xb = xbuf + warp * 16 * Tr::XSTRIDE;
 
     if (threadIdx.x == 0) {
@@ -1238,20 +1041,11 @@ __global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_con
                 alpha_b = alpha_base<Tr>(p, mb);
             }
         }
-        if constexpr (GACC) {
-            // entry q of a column belongs to lane q mod 16 (see gacc_add)
-            float2* ga = reinterpret_cast<float2*>(my_acc);
-            if (lane < 16) {
-                for (int q = lane; q < lena; q += 16) gacc_clear(ga + q);
-                for (int q = lane; q < lenb; q += 16) gacc_clear(ga + lena + q);
-            }
-        } else {
-            for (int i = lane; i < lena + lenb; i += 32) {
-                real2 z;
-                z.x = 0;
-                z.y = 0;
-                my_acc[i] = z;
-            }
+        for (int i = lane; i < lena + lenb; i += 32) {
+            real2 z;
+            z.x = 0;
+            z.y = 0;
+            my_acc[i] = z;
         }
         __syncwarp();
         bool first_flush = true;
@@ -1296,13 +1090,9 @@ __global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_con
                             const int nb = (L - m + 16) >> 4;
                             int sk;
                             if (pole && m < p.pole_mmax)
-                                sk = column_f32x2_pole<K, GACC>(tile, P, m, L, p.pole_ae + p.colstart[m], (float)pole,
+                                sk = column_f32x2_pole<K>(tile, P, m, L, p.pole_ae + p.colstart[m], (float)pole,
                                                            p.pole_rho[m], c ? lcb : lca, c ? lclb : lcla,
                                                            my_acc + (c ? lena : 0), my_xb, lane);
-                            else if constexpr (CH > 0)
-                                sk = column_f32x2v<K, GACC, CH>(tile, P, m, L, p.alpha_f2 + p.colstart[m],
-                                                                c ? lcb : lca, c ? lclb : lcla,
-                                                                my_acc + (c ? lena : 0), my_xb, lane);
                             else
                                 sk = column_f32x2<K>(tile, P, m, L, p.alpha_f2 + p.colstart[m], c ? lcb : lca,
                                                      c ? lclb : lcla, my_acc + (c ? lena : 0), my_xb, lane);
@@ -1316,10 +1106,7 @@ __global__ void __launch_bounds__(W * 32, MINB) analysis_kernel(const __grid_con
                                                my_acc + (c ? lena : 0), my_xb, lane);
                 }
                 if (t == ntiles - 1 || (t + 1) % p.flush_tiles == 0) {
-                    if constexpr (GACC)
-                        flush_gacc(reinterpret_cast<float2*>(my_acc), lena, lenb, ma, mb, L, slot, first_flush, lane);
-                    else
-                        flush_acc<Tr>(my_acc, lena, lenb, ma, mb, L, slot, first_flush, lane);
+                    flush_acc<Tr>(my_acc, lena, lenb, ma, mb, L, slot, first_flush, lane);
                     first_flush = false;
                 }
             }
@@ -1703,17 +1490,15 @@ size_t analysis_smem_bytes(int lmax) {
            (size_t)W * accw * sizeof(typename Tr::real2);
 }
 
-template <typename Tr, int K, int W, bool PACKED = false, bool GACC = false, int CH = 0, int MINB = 1>
+template <typename Tr, int K, int W, bool PACKED = false>
 cudaError_t launch_analysis_t(const AnalysisParams& ap, int sm_count, cudaStream_t st, int* grid_out) {
-    const size_t smem = analysis_smem_bytes<Tr, K, W>(ap.lmax) -
-                        (GACC ? (size_t)W * (((ap.lmax + 2 + 3) & ~3)) * sizeof(typename Tr::real2) : 0);
-    auto kern = analysis_kernel<Tr, K, W, PACKED, GACC, CH, MINB>;
+    const size_t smem = analysis_smem_bytes<Tr, K, W>(ap.lmax);
+    auto kern = analysis_kernel<Tr, K, W, PACKED>;
     int occ = 0;
     cudaError_t e = configure_once(kern, W * 32, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * occ;
-    if (GACC && grid > (int64_t)sm_count * ANALYSIS_GACC_CTAS_PER_SM) grid = (int64_t)sm_count * ANALYSIS_GACC_CTAS_PER_SM;
     if (grid > ap.nunits) grid = ap.nunits;
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = (int)grid;
@@ -1728,8 +1513,7 @@ cudaError_t launch_analysis_t(const AnalysisParams& ap, int sm_count, cudaStream
 int analysis_tile_points(int prec_is_f64, int k32) {
     if (prec_is_f64) return 32 * 4;
     if (k32 == 108) return 32 * 8 * 4;
-    if (k32 == 116 || (k32 >= 118 && k32 <= 122)) return 32 * 16;
-    if (k32 == 124) return 32 * 24;
+    if (k32 == 116) return 32 * 16;
     return 32 * k32;
 }
 
@@ -1740,11 +1524,6 @@ cudaError_t launch_analysis(const AnalysisParams& ap, int prec_is_f64, int k32, 
         case 8: return launch_analysis_t<TraitsF32, 8, 4>(ap, sm_count, st, grid);
         case 12: return launch_analysis_t<TraitsF32, 12, 4>(ap, sm_count, st, grid);
         case 116: return launch_analysis_t<TraitsF32, 16, 4, true>(ap, sm_count, st, grid);
-        case 118: return launch_analysis_t<TraitsF32, 16, 4, true, true, 1, 3>(ap, sm_count, st, grid);
-        case 119: return launch_analysis_t<TraitsF32, 16, 4, true, false, 1, 1>(ap, sm_count, st, grid);
-        case 120: return launch_analysis_t<TraitsF32, 16, 4, true, false, 2, 1>(ap, sm_count, st, grid);
-        case 122: return launch_analysis_t<TraitsF32, 16, 4, true, true, 2, 3>(ap, sm_count, st, grid);
-        case 124: return launch_analysis_t<TraitsF32, 24, 4, true, true, 2, 2>(ap, sm_count, st, grid);
         case 108: return launch_analysis_f32g<8, 4, 4>(ap, sm_count, st, grid);
         default: return launch_analysis_t<TraitsF32, 16, 4>(ap, sm_count, st, grid);
     }

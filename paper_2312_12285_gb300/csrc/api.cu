@@ -322,8 +322,7 @@ extern "C" pointsht_status pointsht_plan_set_timing_events(pointsht_plan plan, v
 
 extern "C" pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, int32_t chunk_log2) {
     if (!plan) return fail(POINTSHT_EINVAL, "set_tuning: plan is NULL");
-    if (!(variant == 0 || variant == 8 || variant == 12 || variant == 16 || variant == 108 || variant == 116 ||
-          variant == 118 || variant == 119 || variant == 120 || variant == 122 || variant == 124))
+    if (!(variant == 0 || variant == 8 || variant == 12 || variant == 16 || variant == 108 || variant == 116))
         return fail(POINTSHT_EINVAL, "set_tuning: unknown variant %d", variant);
     if (!(chunk_log2 == 0 || (chunk_log2 >= 10 && chunk_log2 <= 22)))
         return fail(POINTSHT_EINVAL, "set_tuning: chunk_log2 %d outside {0} or [10, 22]", chunk_log2);
@@ -382,7 +381,7 @@ struct Layout {
     int32_t slot0[PSHT_MAX_FIELDS] = {};
     int64_t unit0[PSHT_MAX_FIELDS] = {};
     // byte offsets in the workspace
-    size_t pts_off = 0, slots_off = 0, counter_off = 0, hist_off = 0, gacc_off = 0, fwd_end = 0;
+    size_t pts_off = 0, slots_off = 0, counter_off = 0, hist_off = 0, fwd_end = 0;
     int64_t nranges = 0;
     size_t gtab_off = 0, bwd_end = 0, shot_off = 0, total = 0;
 };
@@ -423,7 +422,7 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     lo.k32 = 116;
     if (const char* e = getenv("POINTSHT_K")) {
         const int k = atoi(e);
-        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116 || (k >= 118 && k <= 124)) lo.k32 = k;
+        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116) lo.k32 = k;
     }
     if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
@@ -479,10 +478,6 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     for (int c = 0; c < ncat; ++c) lo.nranges += (cats[c].n + SORT_RANGE - 1) / SORT_RANGE;
     lo.hist_off = b;
     b += up256((size_t)std::max<int64_t>(lo.nranges, 1) * SORT_BUCKETS * 8);
-    if (!is_f64 && (lo.k32 == 118 || lo.k32 == 122 || lo.k32 == 124)) {  // rows of every resident (CTA, warp)
-        lo.gacc_off = b;
-        b += up256((size_t)plan->sm_count * ANALYSIS_GACC_CTAS_PER_SM * WARPS * ((L + 2 + 3) & ~3) * 8);
-    }
     lo.fwd_end = b;
     if (is_f64) {  // catalog-order adjoint: the table alone
         lo.gtab_off = 0;
@@ -622,7 +617,6 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
         ap.wait_probe = plan->wait_probe;
         ap.stats = plan->stats;
         ap.slots = reinterpret_cast<double*>(ws + lo.slots_off);
-        ap.gacc = lo.gacc_off ? reinterpret_cast<float2*>(ws + lo.gacc_off) : nullptr;
         ap.counter = reinterpret_cast<int*>(ws + lo.counter_off);
         ap.err = plan->err;
         if (plan->ev_start) CUDA_TRY(cudaEventRecord(plan->ev_start, st));

@@ -22,7 +22,6 @@
 #include <utility>
 
 #define PSHT_MAX_FIELDS 64
-#define ANALYSIS_GACC_CTAS_PER_SM 4   // accumulator rows the workspace holds per SM (variant 118)
 #define PSHT_MAX_CATS 128
 
 namespace psht {
@@ -115,7 +114,6 @@ struct AnalysisParams {
     int32_t pole_mmax;      // ... for orders m < pole_mmax
     int32_t wait_probe;     // test hook: CTA 0 waits on a barrier nothing arrives at, then leaves
     double* slots;          // [slot][nmodes][2]
-    float2* gacc;           // variant 118: accumulator rows [CTA][warp][(lmax + 2 + 3) & ~3]
     unsigned long long* stats;  // optional: [0] += 16-step blocks whose accumulation was skipped, [1] += all
     int* counter;
     unsigned* err;

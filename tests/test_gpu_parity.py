@@ -354,24 +354,3 @@ def test_near_pole_synthesis(dev, near_pole_form):
     print("near-pole form" if near_pole_form else "plain form", err)
     if near_pole_form:
         assert err <= 1e-5, err
-
-
-def test_variant_118_matches_oracle_and_default(dev):
-    """FP32 variant 118 (accumulator rows in global memory, three CTAs per SM)
-    against the oracle, against the default variant, and bit for bit from run
-    to run (each row entry is added to by one lane, in order)."""
-    L = 700
-    wl = catalogs.lognormal_cap(3000, 30000, L, config_id=3, nwaves=64, grid=(128, 256))
-    cats = to_cats(wl, dev)
-    plan = ops.Plan(L, dev)
-    plan.set_tuning(118, 0)
-    a1 = ops.alm_raw(plan, cats, 1, "fp32").cpu().numpy()[0]
-    a2 = ops.alm_raw(plan, cats, 1, "fp32").cpu().numpy()[0]
-    plan.check()
-    assert np.array_equal(a1.view(np.uint64), a2.view(np.uint64))
-    plan.set_tuning(116, 0)
-    a0 = ops.alm_raw(plan, cats, 1, "fp32").cpu().numpy()[0]
-    plan.check()
-    ref = oracle_alm(np_cats(cats), L)
-    assert oracle.rel_err_per_l(a1, ref, L) <= 1e-5
-    assert np.max(np.abs(a1 - a0)) <= 1e-6 * np.max(np.abs(ref))
