@@ -163,6 +163,16 @@ pointsht_status pointsht_plan_set_pole_threshold(pointsht_plan plan, float pole_
  * aligned. */
 pointsht_status pointsht_plan_set_skip_counters(pointsht_plan plan, void* counters);
 
+/* Kernel of the mixed-precision weight-column contraction
+ * (pointsht_alm_columns with POINTSHT_MIXED; the per-m contraction of Eq.
+ * alm_def for several weight columns): 0 = warp-level mma.sync (the
+ * default, the faster one), 1, 2, 3 = fifth-generation tensor cores
+ * (tcgen05.mma, tensor-memory accumulators) with 8 producer warps and 32
+ * multipoles per stage, 4 and 64, 2 and 128.  All split both operands into
+ * fp16 hi + lo and accumulate in FP32; results agree to FP32 rounding.
+ * EINVAL for other values. */
+pointsht_status pointsht_plan_set_mixed_kernel(pointsht_plan plan, int32_t which);
+
 /* Test hook of the bounded waits (the paper has no counterpart).  While
  * enabled, the first CTA of each FP32/FP64 analysis launch waits, bounded, on
  * a shared-memory barrier that no copy and no thread ever arrives at; the

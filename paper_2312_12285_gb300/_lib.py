@@ -22,6 +22,7 @@ EXPORTS = (
     "pointsht_version", "pointsht_last_error", "pointsht_plan_create", "pointsht_plan_destroy",
     "pointsht_plan_lmax", "pointsht_plan_check", "pointsht_plan_set_timing_events", "pointsht_plan_set_tuning",
     "pointsht_plan_set_pole_threshold", "pointsht_plan_set_wait_probe", "pointsht_plan_set_skip_counters",
+    "pointsht_plan_set_mixed_kernel",
     "pointsht_workspace_size",
     "pointsht_alm",
     "pointsht_shot_noise", "pointsht_combine", "pointsht_cl", "pointsht_cl_backward", "pointsht_bin",
@@ -81,6 +82,7 @@ def load(build_if_missing: bool = True):
             "pointsht_plan_set_pole_threshold": ([vp, ctypes.c_float], ctypes.c_int),
             "pointsht_plan_set_wait_probe": ([vp, i32], ctypes.c_int),
             "pointsht_plan_set_skip_counters": ([vp, vp], ctypes.c_int),
+            "pointsht_plan_set_mixed_kernel": ([vp, i32], ctypes.c_int),
             "pointsht_workspace_size": ([vp, cp, i32, i32, ctypes.c_int], sz),
             "pointsht_alm": ([vp, cp, i32, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),
             "pointsht_shot_noise": ([cp, i32, i32, ctypes.c_int, dp, vp, sz, vp], ctypes.c_int),

@@ -57,6 +57,7 @@ int mixed_geometry_arrays();
 int64_t mixed_acc_stride(int);
 cudaError_t launch_mixed_prep(const PrepColsParams&, int64_t, cudaStream_t);
 cudaError_t launch_mixed(const MixedParams&, int, cudaStream_t);
+cudaError_t launch_mixed_tc(const MixedParams&, int, cudaStream_t, int);
 int64_t interp_nranges(int64_t);
 int64_t interp_range();
 cudaError_t launch_interp_sort(const InterpParams&, cudaStream_t);
@@ -80,6 +81,8 @@ struct pointsht_plan_s {
     int pole_mmax = 256;         // ... for orders m < pole_mmax
     float pole_x = 0.9f;         // tiles (warps) whose points all have |x| >= pole_x take the near-pole form
     int wait_probe = 0;          // test hook of the timeout path (pointsht_plan_set_wait_probe)
+    int mixed_kernel = 0;        // weight-column contraction: 0 = mma.sync (default), 1 = tcgen05
+    int tc_shape = 0;            // tcgen05 stage shape: 0 = 8 warps x 32 l, 1 = 4 x 64, 2 = 2 x 128
     unsigned long long* stats = nullptr;  // optional skip counters (pointsht_plan_set_skip_counters)
     double* alpha_d = nullptr;
     int64_t* colstart = nullptr;
@@ -230,14 +233,16 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     std::vector<float4> pae;
     std::vector<float> prho;
     build_tables(lmax, colstart, af, ad, gamma, l2c, pae, prho);
+    af.resize(af.size() + 256, 0.f);  // zeros past the last column, as for the pairs below
     std::vector<float> lh(lmax + 1), ll(lmax + 1);
     for (int m = 0; m <= lmax; ++m) {
         lh[m] = (float)l2c[m];
         ll[m] = (float)(l2c[m] - (double)lh[m]);
     }
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    // 32 zero entries past the last column: kernels read whole 32-step blocks
-    std::vector<float2> af2(af.size() + 32, make_float2(0.f, 0.f));
+    // 256 zero entries past the last column: kernels read whole blocks of up to
+    // 128 steps (the tcgen05 weight-column kernel's widest stage) past a column's end
+    std::vector<float2> af2(af.size() + 256, make_float2(0.f, 0.f));
     for (size_t i = 0; i < af.size(); ++i) af2[i] = make_float2(af[i], af[i]);
     const size_t s_af2 = up(af2.size() * 8);
     const size_t s_af = up(af.size() * 4), s_ad = up(ad.size() * 8), s_cs = up(colstart.size() * 8),
@@ -342,6 +347,14 @@ extern "C" pointsht_status pointsht_plan_set_skip_counters(pointsht_plan plan, v
     if (!plan) return fail(POINTSHT_EINVAL, "set_skip_counters: plan is NULL");
     if ((uintptr_t)counters % 8) return fail(POINTSHT_EINVAL, "set_skip_counters: counters not 8-byte aligned");
     plan->stats = static_cast<unsigned long long*>(counters);
+    return POINTSHT_OK;
+}
+
+extern "C" pointsht_status pointsht_plan_set_mixed_kernel(pointsht_plan plan, int32_t which) {
+    if (!plan) return fail(POINTSHT_EINVAL, "set_mixed_kernel: plan is NULL");
+    if (which < 0 || which > 3) return fail(POINTSHT_EINVAL, "set_mixed_kernel: %d is not in 0..3", which);
+    plan->mixed_kernel = which == 0 ? 0 : 1;
+    plan->tc_shape = which == 0 ? 0 : which - 1;
     return POINTSHT_OK;
 }
 
@@ -809,6 +822,7 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
             mp.wcols = pts + (size_t)(mixed_geometry_arrays() + col0) * c.ntot;
             mp.colmax = colmax + col0;
             mp.alpha2 = plan->alpha_f2;
+            mp.alpha_f = plan->alpha_f;
             mp.colstart = plan->colstart;
             mp.log2c_hi = plan->log2c_hi;
             mp.log2c_lo = plan->log2c_lo;
@@ -819,7 +833,8 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
             mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
             mp.err = plan->err;
             if (plan->ev_start && col0 == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
-            cudaError_t e = launch_mixed(mp, plan->sm_count, st);
+            cudaError_t e = plan->mixed_kernel == 0 ? launch_mixed(mp, plan->sm_count, st)
+                                                    : launch_mixed_tc(mp, plan->sm_count, st, plan->tc_shape);
             if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_columns: mixed launch: %s", cudaGetErrorString(e));
             if (plan->ev_stop && col0 + nc >= ncol) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
         }

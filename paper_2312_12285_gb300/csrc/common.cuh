@@ -210,6 +210,7 @@ struct MixedParams {
     const uint32_t* wcols;    // this pass's first weight array (ncol x ntot)
     const unsigned* colmax;   // this pass's columns
     const float2* alpha2;
+    const float* alpha_f;     // the same coefficients as single floats (tcgen05 kernel)
     const int64_t* colstart;
     const float* log2c_hi;
     const float* log2c_lo;

@@ -77,6 +77,13 @@ class Plan:
         ptr = None if counters is None else ctypes.c_void_p(counters.data_ptr())
         _lib.check(self.lib.pointsht_plan_set_skip_counters(self.handle, ptr), "set_skip_counters")
 
+    def set_mixed_kernel(self, which: str = "mma.sync"):
+        """Weight-column contraction kernel: "mma.sync" (default, faster) or
+        "tcgen05" (= "tcgen05:8x32"; also "tcgen05:4x64", "tcgen05:2x128":
+        producer warps x multipoles per stage)."""
+        code = {"mma.sync": 0, "tcgen05": 1, "tcgen05:8x32": 1, "tcgen05:4x64": 2, "tcgen05:2x128": 3}[which]
+        _lib.check(self.lib.pointsht_plan_set_mixed_kernel(self.handle, code), "set_mixed_kernel")
+
     def set_wait_probe(self, enable: bool):
         """Test hook: the first CTA of each analysis launch gives up a bounded
         wait on a barrier nothing arrives at (see pointsht.h)."""

@@ -1,6 +1,7 @@
 """Weight columns on one point set (pointsht_alm_columns), POINTSHT_MIXED:
 lambda_lm from the FP32 recurrence, the per-m contraction on the tensor cores
-with fp16 hi + lo operands.
+with fp16 hi + lo operands, through both contraction kernels (warp-level
+mma.sync, the default; tcgen05 with tensor-memory accumulators).
 
 Tolerance: pseudo-C_l within 1e-4 of the FP64 oracle, relative to C_l before
 shot-noise subtraction (the mixed-path target; error metric of the C_l
@@ -35,20 +36,27 @@ def _cl_err(a, ref, L):
     return float(np.max(np.abs(c[1:] - r[1:]) / r[1:]))
 
 
-def _columns(dev, x, phi, W, L, precision="mixed"):
+KERNELS = ["tcgen05", "mma.sync"]
+
+
+def _columns(dev, x, phi, W, L, precision="mixed", kernel="mma.sync"):
     plan = ops.get_plan(L, dev)
-    out = ops.alm_columns(plan, torch.from_numpy(x).to(dev), torch.from_numpy(phi).to(dev),
-                          torch.from_numpy(np.ascontiguousarray(W)).to(dev), precision)
-    torch.cuda.synchronize()
-    plan.check()
+    plan.set_mixed_kernel(kernel)
+    try:
+        out = ops.alm_columns(plan, torch.from_numpy(x).to(dev), torch.from_numpy(phi).to(dev),
+                              torch.from_numpy(np.ascontiguousarray(W)).to(dev), precision)
+        torch.cuda.synchronize()
+        plan.check()
+    finally:
+        plan.set_mixed_kernel("mma.sync")
     return out.cpu().numpy()
 
 
 NONZERO = (0, 1, 2, 3, 5, 6, 7, 8, 9)
 
 
-@pytest.fixture(scope="module")
-def small(dev):
+@pytest.fixture(scope="module", params=KERNELS)
+def small(dev, request):
     """25 000 points (24 full tiles and a ragged one) at lmax 256, ten columns
     (two passes: 8 columns, then 2 with the 4-column kernel): the signed FKP
     field, plain weights, weights of order 1e-6 and 1e5 (column scaling), all
@@ -67,26 +75,27 @@ def small(dev):
     W[3] = rng.standard_normal(n) * 1e5
     W[5, :ng] = wl.catalogs[0].w
     W[6:10] = Wj[1:5]
-    got = _columns(dev, x, phi, W, L)
+    kernel = request.param
+    got = _columns(dev, x, phi, W, L, kernel=kernel)
     x64, p64 = x.astype(np.float64), phi.astype(np.float64)
     ref = [oracle.alm(x64, p64, W[f].astype(np.float64), L) if f in NONZERO else None for f in range(10)]
-    return L, x, phi, W, got, ref
+    return L, x, phi, W, got, ref, kernel
 
 
 def test_mixed_matches_oracle(small):
-    L, _, _, _, got, ref = small
+    L, _, _, _, got, ref, _ = small
     for f in NONZERO:
         assert oracle.rel_err_per_l(got[f], ref[f], L) <= TOL_CL, f
         assert _cl_err(got[f], ref[f], L) <= TOL_CL, f
 
 
 def test_zero_column_is_exactly_zero(small):
-    _, _, _, _, got, _ = small
+    _, _, _, _, got, _, _ = small
     assert np.all(got[4] == 0)
 
 
 def test_mixed_matches_plain_fp32_columns(small, dev):
-    L, x, phi, W, got, _ = small
+    L, x, phi, W, got, _, _ = small
     f32 = _columns(dev, x, phi, W, L, "fp32")
     for f in NONZERO:
         assert _cl_err(got[f], f32[f], L) <= TOL_CL, f
@@ -96,8 +105,8 @@ def test_mixed_matches_plain_fp32_columns(small, dev):
 def test_column_result_independent_of_pass_shape(small, dev, cols):
     """A column gives the same a_lm (to FP32 accumulation rounding) whether it
     runs alone, in a 4-column pass or in an 8-column pass."""
-    L, x, phi, W, got, _ = small
-    g = _columns(dev, x, phi, W[cols], L)
+    L, x, phi, W, got, _, kernel = small
+    g = _columns(dev, x, phi, W[cols], L, kernel=kernel)
     for j, f in enumerate(cols):
         assert oracle.rel_err_per_l(g[j], got[f], L) <= 1e-6, f
 
@@ -106,11 +115,11 @@ def test_power_of_two_scaling_is_exact(small, dev):
     """Columns are rescaled by powers of two only: in the same pass layout,
     w * 2^20 gives exactly 2^20 times the a_lm of w (and w * 2^-30 exactly
     2^-30 times), and the other columns are unchanged bit for bit."""
-    L, x, phi, W, got, _ = small
+    L, x, phi, W, got, _, kernel = small
     W2 = W.copy()
     W2[1] *= np.float32(2.0 ** 20)
     W2[6] *= np.float32(2.0 ** -30)
-    g2 = _columns(dev, x, phi, W2, L)
+    g2 = _columns(dev, x, phi, W2, L, kernel=kernel)
     assert np.array_equal(g2[1], got[1] * 2.0 ** 20)
     assert np.array_equal(g2[6], got[6] * 2.0 ** -30)
     for f in (0, 2, 3, 4, 5, 7, 8, 9):
@@ -118,34 +127,38 @@ def test_power_of_two_scaling_is_exact(small, dev):
 
 
 def test_run_to_run_bitwise(small, dev):
-    L, x, phi, W, got, _ = small
-    again = _columns(dev, x, phi, W, L)
+    L, x, phi, W, got, _, kernel = small
+    again = _columns(dev, x, phi, W, L, kernel=kernel)
     assert np.array_equal(again, got)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("n,L", [(5, 64), (1024, 97), (3001, 33), (2049, 1)])
-def test_ragged_sizes_and_odd_lmax(dev, n, L):
+def test_ragged_sizes_and_odd_lmax(dev, n, L, kernel):
     rng = catalogs.rng_for(32, n)
     x = rng.uniform(-1, 1, n).astype(np.float32)
     phi = rng.uniform(0, 2 * np.pi, n).astype(np.float32)
     W = np.stack([rng.uniform(0.5, 1.5, n), rng.standard_normal(n)]).astype(np.float32)
-    got = _columns(dev, x, phi, W, L)
+    got = _columns(dev, x, phi, W, L, kernel=kernel)
     for f in range(2):
         ref = oracle.alm(x.astype(np.float64), phi.astype(np.float64), W[f].astype(np.float64), L)
         assert oracle.rel_err_per_l(got[f], ref, L) <= TOL_CL
         assert np.linalg.norm(got[f] - ref) <= TOL_CL * np.linalg.norm(ref)
 
 
-def test_empty_point_set(dev):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_empty_point_set(dev, kernel):
     e = np.zeros(0, np.float32)
-    got = _columns(dev, e, e, np.zeros((3, 0), np.float32), 40)
+    got = _columns(dev, e, e, np.zeros((3, 0), np.float32), 40, kernel=kernel)
     assert got.shape == (3, oracle.nmodes(40)) and np.all(got == 0)
 
 
-def test_single_point_at_the_pole(dev):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_single_point_at_the_pole(dev, kernel):
     """x = 1: a_lm = 0 for m > 0 and a_l0 = w sqrt((2l+1)/4pi) (Y_lm at the pole)."""
     L = 200
-    got = _columns(dev, np.ones(1, np.float32), np.full(1, 0.7, np.float32), np.full((1, 1), 1.5, np.float32), L)[0]
+    got = _columns(dev, np.ones(1, np.float32), np.full(1, 0.7, np.float32), np.full((1, 1), 1.5, np.float32), L,
+                   kernel=kernel)[0]
     l = np.arange(L + 1)
     assert np.all(got[oracle.index(1, 1, L):] == 0)
     np.testing.assert_allclose(got[:L + 1].real, 1.5 * np.sqrt((2 * l + 1) / (4 * np.pi)), rtol=3e-4)
