@@ -211,7 +211,11 @@ __device__ __forceinline__ float2 mx_fma2_ip(float2 a, float2 b, float2 c) {
 }
 
 // v^(m)_{j alpha} for one interval and 256 orders per warp: lane l holds
-// m = 256 c + l + 32 k, k = 0..7, as (re, im) of the 4 alpha.
+// m = 256 c + l + 32 k, k = 0..7, as (re, im) of the 4 alpha.  The interval's
+// points are read in batches of 32, one point per lane (coalesced), the next
+// batch while the current one runs; the lane that read a point also computes
+// its 32-order phase step, and each point's words reach every lane by
+// shuffles.
 __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ InterpParams p) {
     const int lane = threadIdx.x & 31;
     const int nch = (p.lmax + IP_MCHUNK) / IP_MCHUNK;
@@ -227,46 +231,48 @@ __global__ void __launch_bounds__(256) ip_bin_kernel(const __grid_constant__ Int
         const int64_t r0 = p.binoff[b], r1 = p.binoff[b + 1];
         // orders of this block that exist (the last block of the range may be partial)
         const int kmax = min(8, (p.lmax - IP_MCHUNK * c) / 32 + 1);
-        // the next point's data is loaded one iteration ahead
+        // this lane's point of the next batch
         float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f;
         uint32_t nth = 0u, ntl = 0u;
-        if (r0 < r1) {
-            n0 = p.wc[r0];
-            n1 = p.wc[p.npts + r0];
-            n2 = p.wc[2 * p.npts + r0];
-            n3 = p.wc[3 * p.npts + r0];
-            nth = p.turn[r0];
-            ntl = p.turn[p.npts + r0];
-        }
-        for (int64_t r = r0; r < r1; ++r) {
-            const float2 w01 = make_float2(n0, n1), w23 = make_float2(n2, n3);
-            const uint32_t th = nth, tl = ntl;
-            if (r + 1 < r1) {
-                n0 = p.wc[r + 1];
-                n1 = p.wc[p.npts + r + 1];
-                n2 = p.wc[2 * p.npts + r + 1];
-                n3 = p.wc[3 * p.npts + r + 1];
-                nth = p.turn[r + 1];
-                ntl = p.turn[p.npts + r + 1];
+        auto load = [&](int64_t r) {
+            if (r < r1) {
+                n0 = p.wc[r];
+                n1 = p.wc[p.npts + r];
+                n2 = p.wc[2 * p.npts + r];
+                n3 = p.wc[3 * p.npts + r];
+                nth = p.turn[r];
+                ntl = p.turn[p.npts + r];
             }
-            const float2 nw01 = make_float2(-w01.x, -w01.y), nw23 = make_float2(-w23.x, -w23.y);
-            float cs, sn, c32 = 0.f, s32 = 0.f;
-            phase_f32(m0, th, tl, cs, sn);
-            if (lane == 0) phase_f32(32, th, tl, c32, s32);  // the 32-order step, shared by all lanes
-            c32 = __shfl_sync(0xffffffffu, c32, 0);
-            s32 = __shfl_sync(0xffffffffu, s32, 0);
+        };
+        load(r0 + lane);
+        for (int64_t rb = r0; rb < r1; rb += 32) {
+            const float q0 = n0, q1 = n1, q2 = n2, q3 = n3;
+            const uint32_t qth = nth, qtl = ntl;
+            float qc32, qs32;  // e^{-32 i phi} of this lane's point
+            phase_f32(32, qth, qtl, qc32, qs32);
+            load(rb + 32 + lane);
+            const int cnt = (int)min((int64_t)32, r1 - rb);
+            for (int j = 0; j < cnt; ++j) {
+                const float2 w01 = make_float2(__shfl_sync(0xffffffffu, q0, j), __shfl_sync(0xffffffffu, q1, j));
+                const float2 w23 = make_float2(__shfl_sync(0xffffffffu, q2, j), __shfl_sync(0xffffffffu, q3, j));
+                const uint32_t th = __shfl_sync(0xffffffffu, qth, j), tl = __shfl_sync(0xffffffffu, qtl, j);
+                const float2 nw01 = make_float2(-w01.x, -w01.y), nw23 = make_float2(-w23.x, -w23.y);
+                const float c32 = __shfl_sync(0xffffffffu, qc32, j), s32 = __shfl_sync(0xffffffffu, qs32, j);
+                float cs, sn;
+                phase_f32(m0, th, tl, cs, sn);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (k >= kmax) break;
-                // w c_alpha e^{-i m phi} = w c_alpha (cos - i sin)
-                const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn);
-                vr01[k] = mx_fma2_ip(w01, c2, vr01[k]);
-                vi01[k] = mx_fma2_ip(nw01, s2, vi01[k]);
-                vr23[k] = mx_fma2_ip(w23, c2, vr23[k]);
-                vi23[k] = mx_fma2_ip(nw23, s2, vi23[k]);
-                const float cn = fmaf(cs, c32, -sn * s32);
-                sn = fmaf(sn, c32, cs * s32);
-                cs = cn;
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= kmax) break;
+                    // w c_alpha e^{-i m phi} = w c_alpha (cos - i sin)
+                    const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn);
+                    vr01[k] = mx_fma2_ip(w01, c2, vr01[k]);
+                    vi01[k] = mx_fma2_ip(nw01, s2, vi01[k]);
+                    vr23[k] = mx_fma2_ip(w23, c2, vr23[k]);
+                    vi23[k] = mx_fma2_ip(nw23, s2, vi23[k]);
+                    const float cn = fmaf(cs, c32, -sn * s32);
+                    sn = fmaf(sn, c32, cs * s32);
+                    cs = cn;
+                }
             }
         }
 #pragma unroll
