@@ -145,7 +145,9 @@ pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, in
  * double root and FP32 rounding grows like l^1.5 eps there.  In the FP32
  * analysis (default variant) and the FP32 adjoint / synthesis, a tile (warp)
  * of points that all have x >= pole_x, or all x <= -pole_x, runs the
- * recurrence in Reinsch's difference form on |x| (relative error ~1e-6 of
+ * recurrence of orders m < 256 (at higher orders lambda_lm near the poles
+ * carries sin^m theta and is negligible) in Reinsch's difference form on |x|
+ * (relative error ~1e-6 of
  * the column maximum up to lmax 2048 at any x, instead of up to ~5e-3 at
  * theta ~ 1e-3): one more packed FP32 operation per point and step.  Default
  * 0.9; a value above 1 turns the form off.  EINVAL for values below 0.5 or NaN
