@@ -51,6 +51,9 @@ def parse():
                     help="interp = the interpolated route (samples in theta, default 16 per multipole)")
     ap.add_argument("--columns", type=int, default=0,
                     help="weight columns on the workload's point set (pointsht_alm_columns); 0 = catalog form")
+    ap.add_argument("--mixed-kernel", default="mma.sync", choices=["mma.sync", "tcgen05", "tcgen05:8x32",
+                                                                     "tcgen05:4x64", "tcgen05:2x128"],
+                    help="weight-column contraction kernel of --columns / --precision mixed")
     ap.add_argument("--no-ladder", action="store_true", help="skip the mixed / FP32 / FP64 comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
     ap.add_argument("--no-coupling", action="store_true", help="skip the mode-coupling matrix measurement")
@@ -893,6 +896,7 @@ def ours_columns(args):
     n_rank = xs.shape[0]
     xd, pd, Wd = (torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (xs, ps, Ws))
     plan = ops.get_plan(L, dev)
+    plan.set_mixed_kernel(args.mixed_kernel)
     ws = torch.empty(max(256, ops.workspace_bytes_columns(plan, n_rank, F, prec)), dtype=torch.uint8, device=dev)
     wsn = torch.empty(512 * F + 256, dtype=torch.uint8, device=dev)
     out = torch.empty((F, M), dtype=torch.complex128, device=dev)
@@ -949,9 +953,18 @@ def ours_columns(args):
                "fallback 1.7 PFLOP/s sustained bf16 (fp16 has the bf16 rate)")
         bf16 = bf16 or 1700.0
         per_pass = [min(8, F - 8 * i) for i in range(npass)]
-        achieved = sum(mixed_mma_flops_per_point_mode(c) for c in per_pass) * n_rank * M / (kms / 1e3) / 1e12
+        if args.mixed_kernel == "mma.sync":
+            flops_pm = sum(mixed_mma_flops_per_point_mode(c) for c in per_pass)
+        else:
+            # tcgen05: per 16 points x 32 multipoles two M = 128, N = 32, K = 16 MMAs (hi, lo'),
+            # whatever the number of columns (rows beyond 4 F are zero)
+            flops_pm = npass * 2 * (2 * 128 * 32 * 16) / (16 * 32)
+        achieved = flops_pm * n_rank * M / (kms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16,
-                "traffic": None, "kernel": "analysis_mixed_kernel (mma.sync m16n8k16 fp16 hi+lo, FP32 recurrence)",
+                "traffic": None, "kernel": ("analysis_mixed_kernel (mma.sync m16n8k16 fp16 hi+lo, FP32 recurrence)"
+                                            if args.mixed_kernel == "mma.sync" else
+                                            f"analysis_tc_kernel ({args.mixed_kernel}: tcgen05.mma M=128 fp16 hi+lo, "
+                                            "TMEM accumulators, FP32 recurrence)"),
                 "kernel_ms": kms, "peak_source": src,
                 "note": "tensor flops issued (hi x hi + lo x hi + hi x lo products, 16-row MMAs); the kernel is "
                         "bound by the FP32 recurrence and the fp16 split on the FP32/ALU pipes, not by the tensor pipe"}
