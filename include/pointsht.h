@@ -316,6 +316,10 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
  * paper: in theta y_lm stays smooth through the poles when continued across
  * them (y(-theta) = (-1)^m y(theta)), so the two outer intervals use ghost
  * samples and no point is treated apart.
+ * Several fields: each field is sorted, binned and folded into its own sample
+ * table; fields are taken in groups of up to 4 whose 6 x fields weight
+ * columns share the transform's passes of up to 8 columns (one sample
+ * recurrence per pass instead of one per field).
  * Error: the spline's O(h^4) interpolation error, about 2e-5 relative per
  * value at ntheta = 8 lmax and 1.5e-6 at 16 lmax (h = pi/ntheta), plus the
  * mixed path's rounding; work O(N lmax + ntheta lmax^2) instead of
@@ -323,9 +327,10 @@ pointsht_status pointsht_alm_columns(pointsht_plan plan, const float* x, const f
  * cats as for pointsht_alm with float x, phi, w (POINTSHT_FP32 layout);
  * ntheta even, 2 <= ntheta <= 32768; fewer than 2^31 points per field;
  * alm_out: device, nfield*M complex128; workspace: device, >=
- * pointsht_workspace_size_interp() bytes (~(lmax+1)(ntheta+1) x 48 bytes plus
- * ~52 bytes per point: about 4.3 GB at lmax 2048, ntheta 32768, 1e7 points),
- * 256-byte aligned, clobbered.
+ * pointsht_workspace_size_interp() bytes (per field of a group
+ * ~(lmax+1) ntheta x 16 bytes of sample table, plus ~(lmax+1)(ntheta+1) x 32
+ * bytes and ~52 bytes per point of the largest field: about 4.3 GB at lmax
+ * 2048, ntheta 32768, 1e7 points, one field), 256-byte aligned, clobbered.
  * Errors as for pointsht_alm. */
 size_t pointsht_workspace_size_interp(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
                                       int32_t nfield, int32_t ntheta);

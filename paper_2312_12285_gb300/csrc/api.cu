@@ -856,9 +856,16 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
 }
 
 // ------------------------------------------------------ interpolated --
+// Fields of one interpolated call are transformed in groups of up to
+// INTERP_GROUP: each field of a group is sorted, binned and folded into its
+// own sample table, then the group's 6 x fields weight columns share the
+// transform passes of up to 8 columns (4 fields = 24 columns = 3 full passes).
+constexpr int INTERP_GROUP = 4;
+constexpr int INTERP_COLS = 6;
+
 struct InterpLayout {
-    int64_t npts_max = 0, nranges_max = 0, ntot = 0, chunk = 0, nunits = 0;
-    int32_t nb = 0, nchunk = 0, npairs = 0, maxctas = 0;
+    int64_t npts_max = 0, nranges_max = 0, ntot = 0, chunk = 0, nunits = 0, vtab_fstride = 0;
+    int32_t nb = 0, nchunk = 0, npairs = 0, maxctas = 0, group = 1;
     int64_t accstride = 0;
     size_t hist_off = 0, binoff_off = 0, total_off = 0, wc_off = 0, turn_off = 0, stage_off = 0, v_off = 0,
            vtab_off = 0,
@@ -891,6 +898,8 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
     c.nunits = (int64_t)c.nchunk * c.npairs;
     c.maxctas = 2 * plan->sm_count;
     c.accstride = mixed_acc_stride(L);
+    c.group = std::max(1, std::min(nfield, INTERP_GROUP));
+    c.vtab_fstride = (int64_t)(L + 1) * c.ntot * 4;
     const int64_t np = std::max<int64_t>(c.npts_max, 1);
     size_t b = 0;
     c.hist_off = b;   b += up256((size_t)std::max<int64_t>(c.nranges_max, 1) * c.nb * 4);
@@ -900,13 +909,13 @@ static void make_interp_layout(pointsht_plan plan, const pointsht_catalog* cats,
     c.turn_off = b;   b += up256((size_t)np * 2 * 4);
     c.stage_off = b;  b += up256((size_t)std::max<int64_t>(c.nranges_max, 1) * interp_range() * 7 * 4);
     c.v_off = b;      b += up256((size_t)(L + 1) * c.nb * 4 * 8);
-    c.vtab_off = b;   b += up256((size_t)(L + 1) * c.ntot * 4 * 8);
+    c.vtab_off = b;   b += up256((size_t)c.group * c.vtab_fstride * 8);
     c.nodes_off = b;  b += up256((size_t)c.ntot * mixed_geometry_arrays() * 4);
     c.colmax_off = b; b += 256;
-    c.slots_off = b;  b += up256((size_t)6 * c.nchunk * plan->nmodes * 16);
+    c.slots_off = b;  b += up256((size_t)8 * c.nchunk * plan->nmodes * 16);
     c.acc_off = b;    b += up256((size_t)c.maxctas * c.accstride * 4);
     c.counter_off = b; b += 256;
-    c.T_off = b;      b += up256((size_t)6 * plan->nmodes * 16);
+    c.T_off = b;      b += up256((size_t)INTERP_COLS * c.group * plan->nmodes * 16);
     c.total = b;
 }
 
@@ -953,94 +962,114 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);
     const int L = plan->lmax;
-    for (int f = 0; f < nfield; ++f) {
-        InterpParams ip;
-        memset(&ip, 0, sizeof(ip));
-        ip.lmax = L;
-        ip.ntheta = ntheta;
-        ip.nb = c.nb;
-        ip.ntot = c.ntot;
-        int64_t r = 0, n = 0;
-        for (int k = 0; k < ncat; ++k) {
-            if (cats[k].field != f) continue;
-            ip.cat[ip.ncat].x = static_cast<const float*>(cats[k].x);
-            ip.cat[ip.ncat].phi = static_cast<const float*>(cats[k].phi);
-            ip.cat[ip.ncat].w = static_cast<const float*>(cats[k].w);
-            ip.cat[ip.ncat].n = cats[k].n;
-            ip.cat[ip.ncat].coeff = cats[k].coeff;
+    float2* vtab = reinterpret_cast<float2*>(ws + c.vtab_off);
+    unsigned* colmax = reinterpret_cast<unsigned*>(ws + c.colmax_off);
+    for (int g0 = 0; g0 < nfield; g0 += c.group) {
+        const int gn = std::min(c.group, nfield - g0);
+        CUDA_TRY(cudaMemsetAsync(colmax, 0, 256, st));
+        // ---- per field of the group: sort by interval, bin, fold into its table ----
+        for (int gi = 0; gi < gn; ++gi) {
+            const int f = g0 + gi;
+            InterpParams ip;
+            memset(&ip, 0, sizeof(ip));
+            ip.lmax = L;
+            ip.ntheta = ntheta;
+            ip.nb = c.nb;
+            ip.ntot = c.ntot;
+            int64_t r = 0, n = 0;
+            for (int k = 0; k < ncat; ++k) {
+                if (cats[k].field != f) continue;
+                ip.cat[ip.ncat].x = static_cast<const float*>(cats[k].x);
+                ip.cat[ip.ncat].phi = static_cast<const float*>(cats[k].phi);
+                ip.cat[ip.ncat].w = static_cast<const float*>(cats[k].w);
+                ip.cat[ip.ncat].n = cats[k].n;
+                ip.cat[ip.ncat].coeff = cats[k].coeff;
+                ip.range0[ip.ncat] = r;
+                r += interp_nranges(cats[k].n);
+                n += cats[k].n;
+                ++ip.ncat;
+            }
             ip.range0[ip.ncat] = r;
-            r += interp_nranges(cats[k].n);
-            n += cats[k].n;
-            ++ip.ncat;
+            ip.nranges = r;
+            ip.npts = n;
+            ip.hist = reinterpret_cast<int32_t*>(ws + c.hist_off);
+            ip.binoff = reinterpret_cast<int64_t*>(ws + c.binoff_off);
+            ip.total = reinterpret_cast<int64_t*>(ws + c.total_off);
+            ip.wc = reinterpret_cast<float*>(ws + c.wc_off);
+            ip.turn = reinterpret_cast<uint32_t*>(ws + c.turn_off);
+            ip.stage = reinterpret_cast<uint32_t*>(ws + c.stage_off);
+            ip.v = reinterpret_cast<float2*>(ws + c.v_off);
+            ip.vtab = vtab + (int64_t)gi * c.vtab_fstride;
+            ip.nodes = reinterpret_cast<uint32_t*>(ws + c.nodes_off);
+            ip.colmax = colmax + INTERP_COLS * gi;
+            ip.err = plan->err;
+            if (plan->ev_start && f == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
+            cudaError_t e = launch_interp_sort(ip, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: sort launch: %s", cudaGetErrorString(e));
+            e = launch_interp_tables(ip, plan->sm_count, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: binning launch: %s", cudaGetErrorString(e));
         }
-        ip.range0[ip.ncat] = r;
-        ip.nranges = r;
-        ip.npts = n;
-        ip.hist = reinterpret_cast<int32_t*>(ws + c.hist_off);
-        ip.binoff = reinterpret_cast<int64_t*>(ws + c.binoff_off);
-        ip.total = reinterpret_cast<int64_t*>(ws + c.total_off);
-        ip.wc = reinterpret_cast<float*>(ws + c.wc_off);
-        ip.turn = reinterpret_cast<uint32_t*>(ws + c.turn_off);
-        ip.stage = reinterpret_cast<uint32_t*>(ws + c.stage_off);
-        ip.v = reinterpret_cast<float2*>(ws + c.v_off);
-        ip.vtab = reinterpret_cast<float2*>(ws + c.vtab_off);
-        ip.nodes = reinterpret_cast<uint32_t*>(ws + c.nodes_off);
-        ip.colmax = reinterpret_cast<unsigned*>(ws + c.colmax_off);
-        ip.err = plan->err;
-        CUDA_TRY(cudaMemsetAsync(ip.colmax, 0, 256, st));
-        if (plan->ev_start && f == 0) CUDA_TRY(cudaEventRecord(plan->ev_start, st));
-        cudaError_t e = launch_interp_sort(ip, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: sort launch: %s", cudaGetErrorString(e));
-        e = launch_interp_tables(ip, plan->sm_count, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: binning launch: %s", cudaGetErrorString(e));
-        // transform of the six sample-weight columns (mixed kernel, table mode)
-        CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
-        MixedParams mp;
-        memset(&mp, 0, sizeof(mp));
-        mp.lmax = L;
-        mp.ncol = 6;
-        mp.npairs = c.npairs;
-        mp.flush_tiles = FLUSH_TILES;
-        mp.nmodes = plan->nmodes;
-        mp.chunk = c.chunk;
-        mp.nunits = c.nunits;
-        mp.ntot = c.ntot;
-        mp.nchunk = c.nchunk;
-        mp.pts = ip.nodes;
-        mp.wcols = nullptr;
-        mp.colmax = ip.colmax;
-        mp.alpha2 = plan->alpha_f2;
-        mp.colstart = plan->colstart;
-        mp.log2c_hi = plan->log2c_hi;
-        mp.log2c_lo = plan->log2c_lo;
-        mp.slots = reinterpret_cast<double*>(ws + c.slots_off);
-        mp.accg = reinterpret_cast<float*>(ws + c.acc_off);
-        mp.accstride = c.accstride;
-        mp.maxctas = c.maxctas;
-        mp.vtab = ip.vtab;
-        mp.vtab_h = (float)(3.14159265358979323846 / (double)ntheta);
-        mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
-        mp.err = plan->err;
-        e = launch_mixed(mp, plan->sm_count, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: grid transform launch: %s", cudaGetErrorString(e));
-        ReduceParams rp;
-        memset(&rp, 0, sizeof(rp));
-        rp.nfield = 6;
-        rp.nmodes = plan->nmodes;
-        for (int k = 0; k < 6; ++k) {
-            rp.slot0[k] = k * c.nchunk;
-            rp.nchunk[k] = c.nchunk;
+        // ---- transform of the group's 6 gn sample-weight columns, up to 8 per pass
+        // (mixed kernel, table mode), each pass reduced into its columns of T ----
+        const int ncolg = INTERP_COLS * gn;
+        for (int c0 = 0; c0 < ncolg; c0 += 8) {
+            const int nc = std::min(8, ncolg - c0);
+            CUDA_TRY(cudaMemsetAsync(ws + c.counter_off, 0, 256, st));
+            MixedParams mp;
+            memset(&mp, 0, sizeof(mp));
+            mp.lmax = L;
+            mp.ncol = nc;
+            mp.npairs = c.npairs;
+            mp.flush_tiles = FLUSH_TILES;
+            mp.nmodes = plan->nmodes;
+            mp.chunk = c.chunk;
+            mp.nunits = c.nunits;
+            mp.ntot = c.ntot;
+            mp.nchunk = c.nchunk;
+            mp.pts = reinterpret_cast<const uint32_t*>(ws + c.nodes_off);
+            mp.wcols = nullptr;
+            mp.colmax = colmax + c0;
+            mp.alpha2 = plan->alpha_f2;
+            mp.colstart = plan->colstart;
+            mp.log2c_hi = plan->log2c_hi;
+            mp.log2c_lo = plan->log2c_lo;
+            mp.slots = reinterpret_cast<double*>(ws + c.slots_off);
+            mp.accg = reinterpret_cast<float*>(ws + c.acc_off);
+            mp.accstride = c.accstride;
+            mp.maxctas = c.maxctas;
+            mp.vtab = vtab;
+            mp.vtab_fstride = c.vtab_fstride;
+            mp.tcol0 = c0;
+            mp.vtab_h = (float)(3.14159265358979323846 / (double)ntheta);
+            mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
+            mp.err = plan->err;
+            cudaError_t e = launch_mixed(mp, plan->sm_count, st);
+            if (e != cudaSuccess)
+                return fail(POINTSHT_ECUDA, "alm_interp: grid transform launch: %s", cudaGetErrorString(e));
+            ReduceParams rp;
+            memset(&rp, 0, sizeof(rp));
+            rp.nfield = nc;
+            rp.nmodes = plan->nmodes;
+            for (int k = 0; k < nc; ++k) {
+                rp.slot0[k] = k * c.nchunk;
+                rp.nchunk[k] = c.nchunk;
+            }
+            rp.slots = reinterpret_cast<const double*>(ws + c.slots_off);
+            rp.gamma = plan->gamma;
+            rp.out = reinterpret_cast<double*>(ws + c.T_off) + (size_t)c0 * plan->nmodes * 2;
+            e = launch_reduce(rp, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: reduce launch: %s", cudaGetErrorString(e));
         }
-        rp.slots = reinterpret_cast<const double*>(ws + c.slots_off);
-        rp.gamma = plan->gamma;
-        rp.out = reinterpret_cast<double*>(ws + c.T_off);
-        e = launch_reduce(rp, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: reduce launch: %s", cudaGetErrorString(e));
-        e = launch_interp_combine(L, plan->nmodes, reinterpret_cast<const double*>(ws + c.T_off),
-                                  alm_out + (size_t)f * plan->nmodes * 2, st);
-        if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: combine launch: %s", cudaGetErrorString(e));
-        if (plan->ev_stop && f == nfield - 1) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
+        // ---- per field: a_lm from its six transforms ----
+        for (int gi = 0; gi < gn; ++gi) {
+            const int f = g0 + gi;
+            cudaError_t e = launch_interp_combine(
+                L, plan->nmodes, reinterpret_cast<const double*>(ws + c.T_off) + (size_t)INTERP_COLS * gi * plan->nmodes * 2,
+                alm_out + (size_t)f * plan->nmodes * 2, st);
+            if (e != cudaSuccess) return fail(POINTSHT_ECUDA, "alm_interp: combine launch: %s", cudaGetErrorString(e));
+        }
     }
+    if (plan->ev_stop) CUDA_TRY(cudaEventRecord(plan->ev_stop, st));
     return POINTSHT_OK;
 }
 

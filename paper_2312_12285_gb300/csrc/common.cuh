@@ -219,9 +219,13 @@ struct MixedParams {
     int64_t accstride;
     int32_t maxctas;          // CTAs the accumulator buffer provides for
     float vtab_h;             // table mode: sample spacing h
-    const float2* vtab;       // table mode (interpolated route): [(lmax+1)][ntot][4] = (Vy, Vd) of the north
-                              // and the mirrored south sample at each position; the six columns at order m
-                              // are Vy^(m), h Vd^(m-1), h Vd^(m+1) of each instead of w e^{-i m phi}
+    const float2* vtab;       // table mode (interpolated route): per field [(lmax+1)][ntot][4] = (Vy, Vd) of
+                              // the north and the mirrored south sample at each position; a field's six
+                              // columns at order m are Vy^(m), h Vd^(m-1), h Vd^(m+1) of each instead of
+                              // w e^{-i m phi}
+    int64_t vtab_fstride;     // table mode: float2 entries between two fields' tables
+    int32_t tcol0;            // table mode: column 6 f + j of the group is this pass's column tcol0 + c
+    int32_t pad2_;
     int* counter;
     unsigned* err;
 };

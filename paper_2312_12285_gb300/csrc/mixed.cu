@@ -364,20 +364,23 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                         const int q = 16 * gi + 2 * c4 + (e & 1) + (e >> 1) * 8;
                         float wa, wb = 0.f;
                         if (p.vtab) {
-                            // table mode: columns 3 half + {0: Vy^(m), 1: h Vd^(m-1), 2: h Vd^(m+1)}
-                            // of the sample pair at this position (half 0 north, 1 south)
+                            // table mode: column 6 fg + 3 half + {0: Vy^(m), 1: h Vd^(m-1),
+                            // 2: h Vd^(m+1)} of the group is that of field fg's sample pair at this
+                            // position (half 0 north, 1 south)
                             const int64_t node = pt0 + (int64_t)t * MX_P + qbase + q;
                             auto tab = [&](int c) {
-                                const int half = c >= 3, ty = c - 3 * half;
+                                const int gc = p.tcol0 + c, fg = gc / 6, c6 = gc - 6 * fg;
+                                const int half = c6 >= 3, ty = c6 - 3 * half;
+                                const float2* vt = p.vtab + (int64_t)fg * p.vtab_fstride;
                                 float2 wt = make_float2(0.f, 0.f);
                                 float f = 1.f;
                                 if (ty == 0) {
-                                    wt = p.vtab[((int64_t)m * p.ntot + node) * 4 + 2 * half];
+                                    wt = vt[((int64_t)m * p.ntot + node) * 4 + 2 * half];
                                 } else if (ty == 1 && m >= 1) {
-                                    wt = p.vtab[((int64_t)(m - 1) * p.ntot + node) * 4 + 2 * half + 1];
+                                    wt = vt[((int64_t)(m - 1) * p.ntot + node) * 4 + 2 * half + 1];
                                     f = p.vtab_h;
                                 } else if (ty == 2 && m < L) {
-                                    wt = p.vtab[((int64_t)(m + 1) * p.ntot + node) * 4 + 2 * half + 1];
+                                    wt = vt[((int64_t)(m + 1) * p.ntot + node) * 4 + 2 * half + 1];
                                     f = p.vtab_h;
                                 }
                                 return (comp ? wt.y : wt.x) * f;
@@ -607,9 +610,10 @@ cudaError_t launch_mixed_prep(const PrepColsParams& pp, int64_t nranges, cudaStr
 cudaError_t launch_mixed(const MixedParams& mp, int sm_count, cudaStream_t st) {
     // exactly one weight source: prepared weight arrays or a table
     if ((mp.wcols == nullptr) == (mp.vtab == nullptr) || mp.ncol < 1 || mp.ncol > MX_MAXCOL ||
-        (mp.vtab && mp.ncol != 6))
+        (mp.vtab && (mp.tcol0 < 0 || mp.vtab_fstride < 0)))
         return cudaErrorInvalidValue;
-    const int nf = mp.ncol <= 4 ? 4 : 8;
+    // table mode always runs the 8-column instantiation, whatever this pass's column count
+    const int nf = (mp.vtab || mp.ncol > 4) ? 8 : 4;
     const size_t smem = mixed_smem_bytes(nf);
     // column mode: x from the catalogs; table mode: u = x - 1 of the interpolation samples
     const void* kern = mp.vtab ? reinterpret_cast<const void*>(analysis_mixed_kernel<8, true>)

@@ -97,7 +97,7 @@ def test_fullsize_gradient_vs_central_differences(fullsize):
 def test_fullsize_euler_identity(fullsize):
     wl, cats, loss, cb = fullsize
     s = sum(float((c.w.detach().double() * c.w.grad.double()).sum()) for c in cats)
-    scale = float(torch.abs(cb[0]).double().dot(torch.abs(torch.from_numpy(wl.extra["g_b"]).to(cb.device))))
+    scale = float(torch.abs(cb[0].detach()).double().dot(torch.abs(torch.from_numpy(wl.extra["g_b"]).to(cb.device))))
     assert abs(s - 2.0 * loss) <= 1e-4 * 2.0 * scale
     for c in cats:
         assert torch.isfinite(c.w.grad).all()

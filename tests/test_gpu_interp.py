@@ -133,6 +133,34 @@ def test_two_fields_and_an_empty_one(dev):
     assert np.all(got[2] == 0)
 
 
+def test_six_fields_span_groups_and_passes(dev):
+    """Six fields (transform groups of 4 + 2; passes of 8 columns that span
+    fields), uneven sizes and an empty fifth field: each field against the
+    oracle, and against the same field transformed alone."""
+    L = 48
+    rng = np.random.default_rng(4406)
+    sizes = [5_000, 300, 2_500, 40, 0, 1_200]
+    cats_np = []
+    for f, n in enumerate(sizes):
+        if n == 0:
+            continue
+        x, phi = catalogs.uniform_sphere(rng, n)
+        w = rng.uniform(0.5, 1.5, n).astype(np.float32)
+        cats_np.append((x, phi, w, f, 1.0 - 0.3 * f))
+    cats = [ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (x, phi, w)), f, co)
+            for (x, phi, w, f, co) in cats_np]
+    plan = ops.get_plan(L, dev)
+    nt = 16 * L
+    got = ops.alm_interp(plan, cats, 6, nt).cpu().numpy()
+    plan.check()
+    assert np.all(got[4] == 0)
+    for (x, phi, w, f, co), c in zip(cats_np, cats):
+        ref = oracle.alm_interp(x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64) * co, L, nt)
+        assert oracle.rel_err_per_l(got[f], ref, L) <= 1e-5, f
+        alone = ops.alm_interp(plan, [ops.Cat(c.x, c.phi, c.w, 0, co)], 1, nt).cpu().numpy()[0]
+        assert np.max(np.abs(got[f] - alone)) <= 1e-6 * np.max(np.abs(alone)), f
+
+
 def test_argument_errors(dev):
     wl = catalogs.uniform_fullsky(10, 10, 0.3, 8, np.float32, config_id=44, precision="fp32")
     plan = ops.get_plan(8, dev)
