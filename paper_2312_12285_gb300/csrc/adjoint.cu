@@ -245,19 +245,38 @@ __device__ __forceinline__ float2 adj_mul2(float2 a, float2 b) {
 // range together and a warp all of whose points are below it runs the
 // recurrence only.  Per step and pair: x sigma (mul2), the recurrence (fma2)
 // and the two accumulations (fma2 with (gamma g re, same) and (im, im)).
+// The four warps of a CTA (1024 points; fields are padded to whole CTAs, so a
+// CTA lies in one field) walk the orders and steps together: the table
+// entries, recurrence coefficients and near-pole coefficients of 64 steps at a
+// time are copied into shared memory (cp.async, zero-filled past the column)
+// while the previous 64 steps run, one barrier per 64 steps.
 // The gradient goes back to each point's catalog and index through the
 // prepared point id.
 constexpr int ADJ_KP = 4;                 // f32x2 pairs per lane
 constexpr int ADJ_PW = 32 * 2 * ADJ_KP;   // points per warp (256)
+constexpr int ADJ_WARPS = 4;              // warps per CTA
+constexpr int ADJ_CH = 64;                // steps per staged chunk
 
-__global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_constant__ AdjointParams p) {
+__device__ __forceinline__ void adj_cp_async(void* dst, const void* src, int bytes, bool in) {
+    // bytes 8 or 16; src-size 0 fills the destination with zeros and reads nothing
+    const uint32_t d = smem_u32(dst);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(in ? 8 : 0) : "memory");
+}
+
+__global__ void __launch_bounds__(ADJ_WARPS * 32) adjoint_sorted_kernel(const __grid_constant__ AdjointParams p) {
     constexpr int KP = ADJ_KP, K = 2 * ADJ_KP;
+    __shared__ __align__(16) float4 s_g[2][ADJ_CH];   // (gamma g re, same, gamma g im, same)
+    __shared__ __align__(16) float4 s_pe[2][ADJ_CH];  // near-pole coefficients (a, a, e, e)
+    __shared__ __align__(16) float2 s_a[2][ADJ_CH];   // (alpha, alpha)
     const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t start = gw * ADJ_PW;
-    if (start >= p.ntot) return;
+    const int64_t cta0 = (int64_t)blockIdx.x * ADJ_WARPS * ADJ_PW;
+    const int64_t start = cta0 + (int64_t)(threadIdx.x >> 5) * ADJ_PW;
+    // the launch covers whole CTAs of prepared points: every warp has its 256
     int f = 0;
-    while (f + 1 < p.nfield && p.fld[f + 1].off <= start) ++f;
+    while (f + 1 < p.nfield && p.fld[f + 1].off <= cta0) ++f;
     const float* tf = reinterpret_cast<const float*>(p.pts);
     const uint32_t* tu = p.pts;
     const int64_t N = p.ntot;
@@ -301,6 +320,26 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
 #pragma unroll
     for (int kp = 0; kp < KP; ++kp) u2[kp] = make_float2(fabsf(x2[kp].x) - 1.f, fabsf(x2[kp].y) - 1.f);
 
+    // copy of the 64 steps [64 ch, 64 ch + 64) of order m into buffer b: thread
+    // t < 64 the table entry t, thread 64 + t the coefficients of entry t
+    auto stage = [&](int m, int ch, int b) {
+        const int64_t c0 = p.colstart[m];
+        const int colpad = (int)(p.colstart[m + 1] - c0);
+        const int t = threadIdx.x & (ADJ_CH - 1);
+        const int q = ch * ADJ_CH + t;
+        const bool in = q < colpad;
+        const int64_t e = c0 + (in ? q : 0);
+        if (threadIdx.x < ADJ_CH) {
+            adj_cp_async(&s_g[b][t], gtab + e, 16, in);
+        } else {
+            adj_cp_async(&s_a[b][t], p.alpha2 + e, 8, in);
+            if (m < p.pole_mmax) adj_cp_async(&s_pe[b][t], p.pole_ae + e, 16, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int buf = 0;
+    stage(0, 0, 0);
+
     for (int m = 0; m <= L; ++m) {
         const float lch = p.log2c_hi[m], lcl = p.log2c_lo[m];
         const bool pole_m = pole && m < p.pole_mmax;
@@ -329,96 +368,106 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
         for (int kp = 0; kp < KP; ++kp) ar[kp] = ai[kp] = make_float2(0.f, 0.f);
         bool any_neg = __any_sync(0xffffffffu, lane_neg);
         bool all_dead = __all_sync(0xffffffffu, lane_dead);
-        const int64_t cs0 = p.colstart[m];
-        const float2* al = p.alpha2 + cs0;
-        const float4* gc = gtab + cs0;
         const int nblk = (L - m + 1 + 7) >> 3;
-        const float4* pa = p.pole_ae + cs0;
-        for (int bk = 0; bk < nblk; ++bk) {
-            if (pole_m) {
+        const int nch = (nblk + 7) >> 3;
+        for (int ch = 0; ch < nch; ++ch) {
+            // this thread's copies of chunk (m, ch) are complete; after the barrier
+            // everyone's are, and nobody reads the other buffer any more
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            if (ch + 1 < nch) stage(m, ch + 1, buf ^ 1);
+            else if (m < L) stage(m + 1, 0, buf ^ 1);
+            const float4* gcs = s_g[buf];
+            const float2* als = s_a[buf];
+            const float4* pas = s_pe[buf];
+            const int bend = min(8, nblk - 8 * ch);
+            for (int b = 0; b < bend; ++b) {
+                if (pole_m) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float4 cv[4], gq[4];
+                    for (int h = 0; h < 2; ++h) {
+                        float4 cv[4], gq[4];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        cv[jj] = __ldg(pa + 8 * bk + 4 * h + jj);
-                        gq[jj] = __ldg(gc + 8 * bk + 4 * h + jj);
-                    }
+                        for (int jj = 0; jj < 4; ++jj) {
+                            cv[jj] = pas[8 * b + 4 * h + jj];
+                            gq[jj] = gcs[8 * b + 4 * h + jj];
+                        }
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const float2 a2 = make_float2(cv[jj].x, cv[jj].y), e2 = make_float2(cv[jj].z, cv[jj].w);
-                        const float s = sj[jj];  // q = 8 bk + 4 h + jj = jj (mod 4)
-                        const float2 gr = make_float2(s * gq[jj].x, s * gq[jj].y);
-                        const float2 gi = make_float2(s * gq[jj].z, s * gq[jj].w);
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const float2 a2 = make_float2(cv[jj].x, cv[jj].y), e2 = make_float2(cv[jj].z, cv[jj].w);
+                            const float s = sj[jj];  // q = 8 bk + 4 h + jj = jj (mod 4)
+                            const float2 gr = make_float2(s * gq[jj].x, s * gq[jj].y);
+                            const float2 gi = make_float2(s * gq[jj].z, s * gq[jj].w);
 #pragma unroll
-                        for (int kp = 0; kp < KP; ++kp) {
-                            const float2 c = adj_fma2(a2, u2[kp], e2);
-                            p2[kp] = adj_fma2(c, p1[kp], p2[kp]);
-                            p1[kp] = adj_add2(p1[kp], p2[kp]);
-                            if (!all_dead) {
-                                ar[kp] = adj_fma2(p1[kp], gr, ar[kp]);
-                                ai[kp] = adj_fma2(p1[kp], gi, ai[kp]);
+                            for (int kp = 0; kp < KP; ++kp) {
+                                const float2 c = adj_fma2(a2, u2[kp], e2);
+                                p2[kp] = adj_fma2(c, p1[kp], p2[kp]);
+                                p1[kp] = adj_add2(p1[kp], p2[kp]);
+                                if (!all_dead) {
+                                    ar[kp] = adj_fma2(p1[kp], gr, ar[kp]);
+                                    ai[kp] = adj_fma2(p1[kp], gi, ai[kp]);
+                                }
                             }
                         }
                     }
+                } else {
+                    float4 gv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) gv[j] = gcs[8 * b + j];
+                    float2 av[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) av[j] = als[8 * b + j];
+                    if (all_dead) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+#pragma unroll
+                            for (int kp = 0; kp < KP; ++kp) {
+                                const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
+                                p2[kp] = p1[kp];
+                                p1[kp] = mu;
+                            }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+#pragma unroll
+                            for (int kp = 0; kp < KP; ++kp) {
+                                const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
+                                p2[kp] = p1[kp];
+                                p1[kp] = mu;
+                                ar[kp] = adj_fma2(mu, make_float2(gv[j].x, gv[j].y), ar[kp]);
+                                ai[kp] = adj_fma2(mu, make_float2(gv[j].z, gv[j].w), ai[kp]);
+                            }
+                    }
                 }
-            } else {
-            float4 gv[8];
+                if (any_neg) {
+                    // rescale check every 8 steps (F32Scale; 8-step growth <= 2^42)
+                    lane_neg = false;
+                    lane_dead = true;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) gv[j] = __ldg(gc + 8 * bk + j);
-            float2 av[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) av[j] = __ldg(al + 8 * bk + j);
-            if (all_dead) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                    for (int kp = 0; kp < KP; ++kp) {
-                        const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
-                        p2[kp] = p1[kp];
-                        p1[kp] = mu;
-                    }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                    for (int kp = 0; kp < KP; ++kp) {
-                        const float2 mu = adj_fma2(av[j], adj_mul2(x2[kp], p1[kp]), p2[kp]);
-                        p2[kp] = p1[kp];
-                        p1[kp] = mu;
-                        ar[kp] = adj_fma2(mu, make_float2(gv[j].x, gv[j].y), ar[kp]);
-                        ai[kp] = adj_fma2(mu, make_float2(gv[j].z, gv[j].w), ai[kp]);
-                    }
-            }
-            }
-            if (any_neg) {
-                // rescale check every 8 steps (F32Scale; 8-step growth <= 2^42)
-                lane_neg = false;
-                lane_dead = true;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
-                    float& b = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
-                    if (E[k] < 0 && fmaxf(fabsf(a), fabsf(b)) > 0x1p-61f) {
-                        a *= 0x1p-64f;
-                        b *= 0x1p-64f;
-                        E[k] += 1;
-                        if (E[k] == 0) {  // drop what was summed below range
-                            if (k & 1) {
-                                ar[k >> 1].y = 0.f;
-                                ai[k >> 1].y = 0.f;
-                            } else {
-                                ar[k >> 1].x = 0.f;
-                                ai[k >> 1].x = 0.f;
+                    for (int k = 0; k < K; ++k) {
+                        float& a = (k & 1) ? p1[k >> 1].y : p1[k >> 1].x;
+                        float& bb = (k & 1) ? p2[k >> 1].y : p2[k >> 1].x;
+                        if (E[k] < 0 && fmaxf(fabsf(a), fabsf(bb)) > 0x1p-61f) {
+                            a *= 0x1p-64f;
+                            bb *= 0x1p-64f;
+                            E[k] += 1;
+                            if (E[k] == 0) {  // drop what was summed below range
+                                if (k & 1) {
+                                    ar[k >> 1].y = 0.f;
+                                    ai[k >> 1].y = 0.f;
+                                } else {
+                                    ar[k >> 1].x = 0.f;
+                                    ai[k >> 1].x = 0.f;
+                                }
                             }
                         }
+                        lane_neg |= E[k] < 0;
+                        lane_dead &= E[k] < 0;
                     }
-                    lane_neg |= E[k] < 0;
-                    lane_dead &= E[k] < 0;
+                    any_neg = __any_sync(0xffffffffu, lane_neg);
+                    all_dead = __all_sync(0xffffffffu, lane_dead);
                 }
-                any_neg = __any_sync(0xffffffffu, lane_neg);
-                all_dead = __all_sync(0xffffffffu, lane_dead);
             }
+            buf ^= 1;
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -427,6 +476,7 @@ __global__ void __launch_bounds__(128) adjoint_sorted_kernel(const __grid_consta
             if (E[k] == 0) tot[k] += (double)cs[k] * (double)r - (double)sn[k] * (double)im;
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     const double gn = p.gnoise ? p.gnoise[(int64_t)f * (p.nfield + 1)] : 0.0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -463,7 +513,8 @@ __global__ void build_gtab4_kernel(int L, const double2* __restrict__ galm, cons
     }
 }
 
-int adjoint_sorted_points_per_warp() { return ADJ_PW; }
+// prepared FP32 points of a field are padded to a multiple of this (one CTA)
+int adjoint_sorted_points_per_cta() { return ADJ_WARPS * ADJ_PW; }
 
 cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, const double* gamma, int synth,
                                   cudaStream_t st) {
@@ -472,9 +523,11 @@ cudaError_t launch_adjoint_sorted(const AdjointParams& ap, const double* galm, c
                                              ap.gstride, synth, (float4*)ap.gtab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t nwarps = ap.ntot / ADJ_PW;
-    if (nwarps == 0) return cudaSuccess;
-    adjoint_sorted_kernel<<<(unsigned)((nwarps + 3) / 4), 128, 0, st>>>(ap);
+    // ntot is a multiple of the CTA's 1024 points (every field is padded to it)
+    if (ap.ntot % (ADJ_WARPS * ADJ_PW)) return cudaErrorInvalidValue;
+    const int64_t ncta = ap.ntot / (ADJ_WARPS * ADJ_PW);
+    if (ncta == 0) return cudaSuccess;
+    adjoint_sorted_kernel<<<(unsigned)ncta, ADJ_WARPS * 32, 0, st>>>(ap);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const
                               cudaStream_t);
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
-int adjoint_sorted_points_per_warp();
+int adjoint_sorted_points_per_cta();
 size_t coupling_smem_bytes(int);
 size_t spin2_workspace_bytes(int, const pointsht_shear_catalog*, int, int);
 cudaError_t spin2_run(int, const pointsht_shear_catalog*, int, int, void*, unsigned*, int, double*, double*,
@@ -439,8 +439,8 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
     }
     if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
-    if (!is_f64) {  // fields padded to whole warps of the FP32 adjoint as well
-        const int64_t q = adjoint_sorted_points_per_warp();
+    if (!is_f64) {  // fields padded to whole CTAs of the FP32 adjoint as well
+        const int64_t q = adjoint_sorted_points_per_cta();
         while (lo.P % q) lo.P += analysis_tile_points(is_f64, lo.k32);
     }
     lo.narr = is_f64 ? 4 : 7;
