@@ -314,6 +314,17 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
     // the unit index lives in dynamic shared memory too (no static shared
     // memory, so the launch may use the device's whole opt-in size)
     int& unit_s = *reinterpret_cast<int*>(stage + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS);
+    // [2][16] recurrence coefficients of a block, copied (cp.async) during the
+    // previous block and completed before that block's barrier
+    float4* cst = stage + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS + 1;
+    int cbuf = 0;
+    auto cstage = [&](const float4* src, int b) {
+        if (threadIdx.x < 16) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(cst + b * 16 + threadIdx.x)),
+                         "l"(src + threadIdx.x) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
     int sbuf = 0;  // stage buffer of the next block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t N = p.ntot;
@@ -334,10 +345,12 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
         const int len = L - l0 + 1;
         if (len <= 0) continue;
         const int nblk = (len + 15) >> 4;
+        const float4* coef = p.coef + (int64_t)m * p.cstride;  // nblk * 16 <= cstride entries
+        cstage(coef, cbuf);  // block 0 of the first round
         for (int q = threadIdx.x; q < nblk * 16; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         const float4 sc = p.seedc[m];
-        const float4* coef = p.coef + (int64_t)m * p.cstride;
         const double* rowscale = p.scale + (int64_t)m * p.cstride;
         double4* slot = p.slots + (int64_t)ci * p.nmodes + tri_base(m, L) + l0;
         const int nround = ch.n / S2_ROUND;
@@ -368,12 +381,16 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
             bool any_neg = __any_sync(0xffffffffu, lane_neg);
             bool all_dead = __all_sync(0xffffffffu, lane_dead);
             for (int bk = 0; bk < nblk; ++bk) {
-                const float4* cb = coef + bk * 16;
+                const float4* cb = cst + cbuf * 16;
+                // the next block's coefficients into the other buffer (read by every
+                // warp before the previous block's barrier, so free)
+                if (bk + 1 < nblk) cstage(coef + (bk + 1) * 16, cbuf ^ 1);
+                else if (r + 1 < nround) cstage(coef, cbuf ^ 1);
                 const bool skip = all_dead;
                 if (skip) {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c = __ldg(cb + j);
+                        const float4 c = cb[j];
                         const float2 A2 = make_float2(c.x, c.y), B2 = make_float2(c.z, c.w);
 #pragma unroll
                         for (int k = 0; k < S2_K; ++k) {
@@ -386,7 +403,7 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
                 } else {
 #pragma unroll 4
                     for (int j = 0; j < 16; ++j) {
-                        const float4 c = __ldg(cb + j);
+                        const float4 c = cb[j];
                         const float2 A2 = make_float2(c.x, c.y), B2 = make_float2(c.z, c.w);
                         float2 ra = make_float2(0.f, 0.f), ia = ra, rb = ra, ib = ra;
 #pragma unroll
@@ -479,6 +496,7 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
                 // the buffer is written again.
                 float4* sb = stage + sbuf * S2_WARPS * 16;
                 if (half == 0) sb[warp * 16 + row] = s;
+                asm volatile("cp.async.wait_group 0;" ::: "memory");  // the next block's coefficients
                 __syncthreads();
                 if (threadIdx.x < 64) {
                     const int q = threadIdx.x >> 2, comp = threadIdx.x & 3;
@@ -488,6 +506,7 @@ __global__ void __launch_bounds__(S2_WARPS * 32, 3) s2_analysis_kernel(const __g
                     reinterpret_cast<float*>(acc)[(bk * 16 + q) * 4 + comp] += v;
                 }
                 sbuf ^= 1;
+                cbuf ^= 1;
             }
             if ((r + 1) % S2_FLUSH == 0 || r + 1 == nround) {
                 __syncthreads();  // the last block's combine is in acc
@@ -611,7 +630,7 @@ static bool spin2_layout(int L, const S2Catalog* cats, int ncat, int nfield, S2L
 }
 
 static size_t spin2_smem_bytes(int L) {
-    return (size_t)(L + 17 + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS + 1) * 16;
+    return (size_t)(L + 17 + 2 * S2_WARPS * 16 + S2_WARPS * 16 * S2_XS + 1 + 2 * 16) * 16;
 }
 
 static cudaError_t launch_spin2(int L, const S2Catalog* cats, int ncat, int nfield, const S2Layout& lo, char* ws,
