@@ -269,6 +269,37 @@ def test_adjoint_several_catalogs_and_fields(dev, prec):
         assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
 
 
+def test_adjoint_fields_at_cta_boundaries(dev):
+    """FP32 adjoint with five fields of 1, 1023, 1024, 1025 and 3000 points
+    (fields are padded to whole 1024-point CTAs, whose four warps share the
+    staged coefficient chunks), one of them with every point near the north
+    pole (near-pole form for m < 256), lmax 300 (several 64-step chunks per
+    order): each gradient against the oracle."""
+    L = 300
+    rng = np.random.default_rng(29)
+    sizes = [1, 1023, 1024, 1025, 3000]
+    raw = []
+    for f, n in enumerate(sizes):
+        x = rng.uniform(0.95, 1.0, n) if f == 2 else rng.uniform(-1, 1, n)
+        raw.append((x, rng.uniform(0, 6.28, n), rng.uniform(0.5, 1.5, n)))
+    coeffs = [1.0, -0.4, 0.8, 1.3, -1.1]
+    cats = [ops.Cat(*(torch.from_numpy(v.astype(np.float32)).to(dev) for v in r), f, c)
+            for f, (r, c) in enumerate(zip(raw, coeffs))]
+    M = oracle.nmodes(L)
+    nf = len(sizes)
+    g = rng.standard_normal((nf, M)) + 1j * rng.standard_normal((nf, M))
+    gn = np.diag(rng.uniform(-0.5, 0.5, nf))
+    plan = ops.get_plan(L, dev)
+    grads = ops.alm_backward_raw(plan, cats, nf, "fp32", torch.from_numpy(g).to(dev), torch.from_numpy(gn).to(dev))
+    torch.cuda.synchronize()
+    plan.check()
+    for f, ((x, p, w), c, gw) in enumerate(zip(raw, coeffs, grads)):
+        got = gw.double().cpu().numpy()
+        xs, ps, ws = (v.astype(np.float32).astype(np.float64) for v in (x, p, w))
+        ref = c * oracle.adjoint(xs, ps, g[f], L) + 2 * c * c * ws * gn[f, f] / FOUR_PI
+        assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref)), f
+
+
 def test_autograd_binned_cl_gradient(dev):
     """Differentiation config structure (small): d(sum_b g_b C_b)/dw via the
     adjoint kernel vs the oracle's definition-level gradient."""
