@@ -432,11 +432,7 @@ static pointsht_status make_layout(pointsht_plan plan, const pointsht_catalog* c
                                    pointsht_precision prec, Layout& lo) {
     const int is_f64 = prec == POINTSHT_FP64;
     lo.is_f64 = is_f64;
-    lo.k32 = 116;
-    if (const char* e = getenv("POINTSHT_K")) {
-        const int k = atoi(e);
-        if (k == 8 || k == 12 || k == 16 || k == 108 || k == 116) lo.k32 = k;
-    }
+    lo.k32 = 116;  // the default FP32 variant; pointsht_plan_set_tuning selects another
     if (plan->variant) lo.k32 = plan->variant;
     lo.P = analysis_tile_points(is_f64, lo.k32);
     if (!is_f64) {  // fields padded to whole CTAs of the FP32 adjoint as well
