@@ -1036,6 +1036,14 @@ extern "C" pointsht_status pointsht_alm_interp(pointsht_plan plan, const pointsh
             mp.vtab = vtab;
             mp.vtab_fstride = c.vtab_fstride;
             mp.tcol0 = c0;
+            // near-pole form of the sample recurrence for the positions next to the
+            // north pole: the positions are in theta order, so a warp's 128 span a
+            // theta range, and the threshold is min(pole_x, 0.75) (the form is at
+            // least as accurate as the standard one from x = 0.7 up)
+            mp.pole_ae = plan->pole_x <= 1.f ? plan->pole_ae : nullptr;
+            mp.pole_rho = plan->pole_rho;
+            mp.pole_x = std::min(plan->pole_x, 0.75f);
+            mp.pole_mmax = std::min(plan->pole_mmax, 64);
             mp.vtab_h = (float)(3.14159265358979323846 / (double)ntheta);
             mp.counter = reinterpret_cast<int*>(ws + c.counter_off);
             mp.err = plan->err;

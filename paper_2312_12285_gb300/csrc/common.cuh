@@ -225,7 +225,11 @@ struct MixedParams {
                               // w e^{-i m phi}
     int64_t vtab_fstride;     // table mode: float2 entries between two fields' tables
     int32_t tcol0;            // table mode: column 6 f + j of the group is this pass's column tcol0 + c
-    int32_t pad2_;
+    int32_t pole_mmax;        // table mode: near-pole form for orders m < pole_mmax ...
+    float pole_x;             // ... in warps whose positions all have x >= pole_x
+    int32_t pad3_;
+    const float4* pole_ae;    // near-pole coefficients (a, a, e, e) in the column layout (NULL: off)
+    const float* pole_rho;    // per order: the odd-step factor of the near-pole normalisation
     int* counter;
     unsigned* err;
 };

@@ -135,6 +135,13 @@ __device__ __forceinline__ float2 mx_mul2(float2 a, float2 b) {
         : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
     return d;
 }
+__device__ __forceinline__ float2 mx_add2(float2 a, float2 b) {
+    float2 d;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(reinterpret_cast<unsigned long long&>(d))
+        : "l"(reinterpret_cast<unsigned long long&>(a)), "l"(reinterpret_cast<unsigned long long&>(b)));
+    return d;
+}
 // two f32 -> packed f16x2 with `a` in the low half, saturating to the finite range
 __device__ __forceinline__ uint32_t mx_pack(float a, float b) {
     uint32_t r;
@@ -204,6 +211,69 @@ __device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&
             const float2 sg = mx_fma2(av1, UF ? mx_fma2(u2[kp], p1[kp], p1[kp]) : mx_mul2(u2[kp], p1[kp]), p2[kp]);
             p2[kp] = p1[kp];
             p1[kp] = sg;
+        }
+        if (SPLIT) {
+#pragma unroll
+            for (int kp = 0; kp < 2; ++kp) {
+                const float hax = __uint_as_float(__float_as_uint(s0[kp].x) & mask[2 * kp]);
+                const float hay = __uint_as_float(__float_as_uint(s0[kp].y) & mask[2 * kp + 1]);
+                const float hbx = __uint_as_float(__float_as_uint(p1[kp].x) & mask[2 * kp]);
+                const float hby = __uint_as_float(__float_as_uint(p1[kp].y) & mask[2 * kp + 1]);
+                const float2 la = mx_fma2(s0[kp], nal[kp], make_float2(hax, hay));
+                const float2 lb = mx_fma2(p1[kp], nal[kp], make_float2(hbx, hby));
+                hi[2 * kp][j2] = mx_pack(hax, hbx);
+                hi[2 * kp + 1][j2] = mx_pack(hay, hby);
+                lo[2 * kp][j2] = mx_pack(la.x, lb.x);
+                lo[2 * kp + 1][j2] = mx_pack(la.y, lb.y);
+            }
+        }
+    }
+}
+
+// The same round in the near-pole form (table mode, positions next to the
+// north pole, orders m < pole_mmax): Reinsch's difference form of the
+// recurrence in the smooth normalisation of the near-pole table, on
+// u = x - 1: per step and pair c = a u + e, d = c y + d, y = y + d, with
+// (p1, p2) holding (y, d).  y is the value that is split and staged; the
+// normalisation's step factor s_q (q odd ? rho : 1) is applied to the sums.
+// alr: the round's table entries 0..3 (a, a, e, e); cv4: entries 4..7.
+template <bool SPLIT>
+__device__ __forceinline__ void mx_round_pole(const float4 (&alr)[4], const float4* __restrict__ cv4,
+                                              const float2 (&u2)[2], float2 (&p1)[2], float2 (&p2)[2],
+                                              const float2 (&nal)[2], const uint32_t (&mask)[4],
+                                              uint32_t (&hi)[4][4], uint32_t (&lo)[4][4]) {
+    // entries 0..3 were fetched a round ahead (alr); 4..7 are fetched two at a
+    // time, each pair one step pair ahead of its use
+    float4 cn0 = __ldg(cv4), cn1 = __ldg(cv4 + 1);
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+        float4 ca, cb;
+        if (j2 < 2) {
+            ca = alr[2 * j2];
+            cb = alr[2 * j2 + 1];
+        } else {
+            ca = cn0;
+            cb = cn1;
+            if (j2 == 2) {
+                cn0 = __ldg(cv4 + 2);
+                cn1 = __ldg(cv4 + 3);
+            }
+        }
+        const float2 a0 = make_float2(ca.x, ca.y), e0 = make_float2(ca.z, ca.w);
+        const float2 a1 = make_float2(cb.x, cb.y), e1 = make_float2(cb.z, cb.w);
+        float2 s0[2];
+#pragma unroll
+        for (int kp = 0; kp < 2; ++kp) {
+            const float2 c = mx_fma2(a0, u2[kp], e0);
+            p2[kp] = mx_fma2(c, p1[kp], p2[kp]);
+            p1[kp] = mx_add2(p1[kp], p2[kp]);
+            s0[kp] = p1[kp];
+        }
+#pragma unroll
+        for (int kp = 0; kp < 2; ++kp) {
+            const float2 c = mx_fma2(a1, u2[kp], e1);
+            p2[kp] = mx_fma2(c, p1[kp], p2[kp]);
+            p1[kp] = mx_add2(p1[kp], p2[kp]);
         }
         if (SPLIT) {
 #pragma unroll
@@ -353,6 +423,18 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     }
                     mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
                 }
+                // table mode: near-pole form when every position of the warp has
+                // x >= pole_x (u = x - 1 is what the tile holds; padding has u = -1)
+                const float umin = p.pole_x - 1.f;
+                const bool pole = UF && p.pole_ae != nullptr && m < p.pole_mmax &&
+                                  __all_sync(0xffffffffu, (u2[0].x >= umin) & (u2[0].y >= umin) &
+                                                              (u2[1].x >= umin) & (u2[1].y >= umin));
+                const float4* pae = pole ? p.pole_ae + p.colstart[m] : nullptr;
+                // step factor s_q (q odd ? rho : 1) of the near-pole normalisation; this
+                // lane's sums are of steps q = 2 c4 + (e & 1) (mod 4)
+                const float rho = pole ? p.pole_rho[m] : 1.f;
+                const float fac_even = pole ? ((c4 & 1) ? -1.f : 1.f) : 1.f;
+                const float fac_odd = pole ? ((c4 & 1) ? -rho : rho) : 1.f;
                 __syncwarp();
                 // ---- A fragments ----
                 uint32_t A[8][AR];
@@ -426,10 +508,14 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                 const int nrounds = 4 * ((len + MX_BLK - 1) / MX_BLK);
                 float D1[4], D2[4];
                 float accv[ITEMS];
-                // recurrence coefficients of the next round, loaded one round ahead
+                // recurrence coefficients of the next round, loaded one round ahead:
+                // 4 float4 per round, the (alpha, alpha) pairs of 8 steps, or the first
+                // 4 near-pole entries (a, a, e, e)
                 float4 aln[4];
+                const float4* apf = pole ? pae : reinterpret_cast<const float4*>(alpha2);
+                const int astride = pole ? 8 : 4;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) aln[j] = __ldg(reinterpret_cast<const float4*>(alpha2) + j);
+                for (int j = 0; j < 4; ++j) aln[j] = __ldg(apf + j);
                 // Rounds of 8 steps in a three-stage pipeline.  Iteration r8:
                 //   store the sums of round r8-2 (its MMAs were issued one iteration ago),
                 //   load the B fragments of round r8-1 and issue its MMAs in the same
@@ -446,6 +532,11 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                         if (NF == 4) {
                             pb[row * PS + g] = mm_prev ? (D1[0] - D2[0]) + D1[2] : 0.f;
                             pb[(row + 1) * PS + g] = mm_prev ? (D1[1] - D2[1]) + D1[3] : 0.f;
+                        } else if (pole) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                pb[(row + (e & 1)) * PS + (e >> 1) * 8 + g] =
+                                    mm_prev ? (D1[e] - D2[e]) * ((e & 1) ? fac_odd : fac_even) : 0.f;
                         } else {
 #pragma unroll
                             for (int e = 0; e < 4; ++e)
@@ -496,7 +587,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     if (r8 + 1 < nrounds) {
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            aln[j] = __ldg(reinterpret_cast<const float4*>(alpha2 + 8 * (r8 + 1)) + j);
+                            aln[j] = __ldg(apf + astride * (r8 + 1) + j);
                     }
                     uint32_t hi[4][4], lo[4][4];
                     auto mmas = [&]() {
@@ -523,14 +614,28 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                             }
                         }
                     };
-                    if (mm && act) {
-                        mmas();
-                        mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
-                    } else if (act) {
-                        mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
+                    // (each form in its own branch, so that the MMAs and the round's
+                    // FP32 work stay in one basic block)
+                    if (pole) {
+                        if (mm && act) {
+                            mmas();
+                            mx_round_pole<true>(alr, pae + 8 * r8 + 4, u2, p1, p2, nal, mask, hi, lo);
+                        } else if (act) {
+                            mx_round_pole<true>(alr, pae + 8 * r8 + 4, u2, p1, p2, nal, mask, hi, lo);
+                        } else {
+                            if (mm) mmas();
+                            if (have) mx_round_pole<false>(alr, pae + 8 * r8 + 4, u2, p1, p2, nal, mask, hi, lo);
+                        }
                     } else {
-                        if (mm) mmas();
-                        if (have) mx_round<false, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        if (mm && act) {
+                            mmas();
+                            mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        } else if (act) {
+                            mx_round<true, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        } else {
+                            if (mm) mmas();
+                            if (have) mx_round<false, UF>(alr, u2, p1, p2, nal, mask, hi, lo);
+                        }
                     }
                     if (act) {
 #pragma unroll
