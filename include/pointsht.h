@@ -150,8 +150,8 @@ pointsht_status pointsht_plan_set_tuning(pointsht_plan plan, int32_t variant, in
  * (relative error ~1e-6 of
  * the column maximum up to lmax 2048 at any x, instead of up to ~5e-3 at
  * theta ~ 1e-3): one more packed FP32 operation per point and step.  The
- * interpolated route's sample transform uses the same form for warps whose
- * sample positions all have x >= min(pole_x, 0.75).  Default 0.9; a value
+ * interpolated route's sample transform uses the same form, for orders
+ * m < 64, in warps whose sample positions all have x >= min(pole_x, 0.75).  Default 0.9; a value
  * above 1 turns the form off everywhere.  EINVAL for values below 0.5 or NaN
  * (the form is less accurate than the standard one near x = 0). */
 pointsht_status pointsht_plan_set_pole_threshold(pointsht_plan plan, float pole_x);
