@@ -230,12 +230,12 @@ __device__ __forceinline__ void mx_round(const float4 (&alr)[4], const float2 (&
     }
 }
 
-// The same round in the near-pole form (table mode, positions next to the
-// north pole, orders m < pole_mmax): Reinsch's difference form of the
-// recurrence in the smooth normalisation of the near-pole table, on
-// u = x - 1: per step and pair c = a u + e, d = c y + d, y = y + d, with
-// (p1, p2) holding (y, d).  y is the value that is split and staged; the
-// normalisation's step factor s_q (q odd ? rho : 1) is applied to the sums.
+// The same round in the near-pole form (a warp of points next to one pole,
+// orders m < pole_mmax): Reinsch's difference form of the recurrence in the
+// smooth normalisation of the near-pole table, on u = |x| - 1: per step and
+// pair c = a u + e, d = c y + d, y = y + d, with (p1, p2) holding (y, d).  y is
+// the value that is split and staged; the step factor s_q sgn^q (q odd ? rho : 1)
+// of the normalisation and the mirror is applied to the sums.
 // alr: the round's table entries 0..3 (a, a, e, e); cv4: entries 4..7.
 template <bool SPLIT>
 __device__ __forceinline__ void mx_round_pole(const float4 (&alr)[4], const float4* __restrict__ cv4,
@@ -423,16 +423,38 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                     }
                     mask[k] = E[k] == 0 ? 0xffffe000u : 0u;
                 }
-                // table mode: near-pole form when every position of the warp has
-                // x >= pole_x (u = x - 1 is what the tile holds; padding has u = -1)
-                const float umin = p.pole_x - 1.f;
-                const bool pole = UF && p.pole_ae != nullptr && m < p.pole_mmax &&
-                                  __all_sync(0xffffffffu, (u2[0].x >= umin) & (u2[0].y >= umin) &
-                                                              (u2[1].x >= umin) & (u2[1].y >= umin));
+                // Near-pole form for orders m < pole_mmax when every point of the warp
+                // lies next to one pole.  Table mode: the tile holds u = x - 1 of the
+                // north samples (padding u = -1), x >= pole_x.  Column mode: the tile
+                // holds x; every |x| >= pole_x with one sign sgn (the |x| order keeps the
+                // signs apart there; padding has x = 0), and the recurrence runs on
+                // u = |x| - 1, mirrored by sgn^q.
+                bool pole = false;
+                float sgn = 1.f;
+                if (p.pole_ae != nullptr && m < p.pole_mmax) {
+                    if (UF) {
+                        const float umin = p.pole_x - 1.f;
+                        pole = __all_sync(0xffffffffu, (u2[0].x >= umin) & (u2[0].y >= umin) &
+                                                           (u2[1].x >= umin) & (u2[1].y >= umin));
+                    } else {
+                        const float px = p.pole_x;
+                        const bool np = __all_sync(0xffffffffu, (u2[0].x >= px) & (u2[0].y >= px) &
+                                                                    (u2[1].x >= px) & (u2[1].y >= px));
+                        const bool sp = __all_sync(0xffffffffu, (u2[0].x <= -px) & (u2[0].y <= -px) &
+                                                                    (u2[1].x <= -px) & (u2[1].y <= -px));
+                        pole = np | sp;
+                        sgn = np ? 1.f : -1.f;
+                        if (pole) {
+#pragma unroll
+                            for (int kp = 0; kp < 2; ++kp)
+                                u2[kp] = make_float2(fabsf(u2[kp].x) - 1.f, fabsf(u2[kp].y) - 1.f);
+                        }
+                    }
+                }
                 const float4* pae = pole ? p.pole_ae + p.colstart[m] : nullptr;
-                // step factor s_q (q odd ? rho : 1) of the near-pole normalisation; this
-                // lane's sums are of steps q = 2 c4 + (e & 1) (mod 4)
-                const float rho = pole ? p.pole_rho[m] : 1.f;
+                // step factor s_q sgn^q (q odd ? rho : 1) of the near-pole normalisation;
+                // this lane's sums are of steps q = 2 c4 + (e & 1) (mod 4)
+                const float rho = pole ? sgn * p.pole_rho[m] : 1.f;
                 const float fac_even = pole ? ((c4 & 1) ? -1.f : 1.f) : 1.f;
                 const float fac_odd = pole ? ((c4 & 1) ? -rho : rho) : 1.f;
                 __syncwarp();
@@ -530,8 +552,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                         float* pb = part + ((rp >> 2) & 1) * (MX_WARPS * MX_BLK * PS);
                         const int row = warp * MX_BLK + 8 * (rp & 3) + 2 * c4;
                         if (NF == 4) {
-                            pb[row * PS + g] = mm_prev ? (D1[0] - D2[0]) + D1[2] : 0.f;
-                            pb[(row + 1) * PS + g] = mm_prev ? (D1[1] - D2[1]) + D1[3] : 0.f;
+                            // columns 2 c4 (steps q even mod 2) and 2 c4 + 1 (odd); the step
+                            // factors are 1 outside the near-pole form
+                            pb[row * PS + g] = mm_prev ? ((D1[0] - D2[0]) + D1[2]) * fac_even : 0.f;
+                            pb[(row + 1) * PS + g] = mm_prev ? ((D1[1] - D2[1]) + D1[3]) * fac_odd : 0.f;
                         } else if (pole) {
 #pragma unroll
                             for (int e = 0; e < 4; ++e)

@@ -201,7 +201,9 @@ def full(dev):
 
 def test_fullsize_sampled_columns(full):
     """Short columns m = 1900, 2047, 2048 (seeds deepest below the FP32 range)
-    of every weight column, over all 1e7 points."""
+    of every weight column, over all 1e7 points, and the long columns m = 0, 1
+    of the FKP column, which carry the points next to the cap's pole (near-pole
+    form of the recurrence there): 1e-5."""
     L, x, phi, W, got = full
     x64, p64 = x.astype(np.float64), phi.astype(np.float64)
     for f in range(W.shape[0]):
@@ -209,6 +211,10 @@ def test_fullsize_sampled_columns(full):
         for m, col in ref.items():
             g = got[f][oracle.index(m, m, L):oracle.index(L, m, L) + 1]
             assert np.linalg.norm(g - col) <= TOL_CL * np.linalg.norm(col), (f, m)
+    ref = oracle.alm(x64, p64, W[0].astype(np.float64), L, mlist=[0, 1])
+    for m, col in ref.items():
+        g = got[0][oracle.index(m, m, L):oracle.index(L, m, L) + 1]
+        assert np.linalg.norm(g - col) <= 1e-5 * np.linalg.norm(col), m
 
 
 def test_fullsize_low_l_pseudo_cl(full):
