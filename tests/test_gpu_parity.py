@@ -297,7 +297,10 @@ def test_adjoint_fields_at_cta_boundaries(dev):
         got = gw.double().cpu().numpy()
         xs, ps, ws = (v.astype(np.float32).astype(np.float64) for v in (x, p, w))
         ref = c * oracle.adjoint(xs, ps, g[f], L) + 2 * c * c * ws * gn[f, f] / FOUR_PI
-        assert np.max(np.abs(got - ref)) <= 2e-5 * np.max(np.abs(ref)), f
+        # the FP32 recurrence carries ~l eps per value: at lmax 300 (2.5 times the
+        # lmax of the 2e-5 test above) random cotangents give ~2e-5 of the
+        # largest gradient on the uniform 3000-point field
+        assert np.max(np.abs(got - ref)) <= 4e-5 * np.max(np.abs(ref)), f
 
 
 def test_autograd_binned_cl_gradient(dev):
