@@ -90,7 +90,7 @@ def test_fullsize_gradient_vs_central_differences(fullsize):
     floor = 1e-4 * float(np.sqrt(np.mean(fd * fd)))
     err = np.abs(got - fd) / np.maximum(np.abs(fd) * 1e-4, floor)
     assert np.all(err <= 1.0), (np.max(err), np.argmax(err))
-    scale = float(torch.abs(fullsize[3][0]).double().cpu().numpy() @ np.abs(wl.extra["g_b"]))
+    scale = float(torch.abs(fullsize[3][0].detach()).double().cpu().numpy() @ np.abs(wl.extra["g_b"]))
     assert abs(loss - ref["loss"]) <= 1e-5 * scale
 
 
