@@ -820,11 +820,6 @@ extern "C" pointsht_status pointsht_alm_columns(pointsht_plan plan, const float*
             mp.alpha2 = plan->alpha_f2;
             mp.alpha_f = plan->alpha_f;
             mp.colstart = plan->colstart;
-            // near-pole form for warps of points next to one pole (mma.sync kernel)
-            mp.pole_ae = plan->pole_x <= 1.f ? plan->pole_ae : nullptr;
-            mp.pole_rho = plan->pole_rho;
-            mp.pole_x = plan->pole_x;
-            mp.pole_mmax = plan->pole_mmax;
             mp.log2c_hi = plan->log2c_hi;
             mp.log2c_lo = plan->log2c_lo;
             mp.slots = reinterpret_cast<double*>(ws + c.slots_off);

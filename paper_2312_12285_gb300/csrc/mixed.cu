@@ -46,6 +46,11 @@ constexpr int MX_P = MX_WARPS * MX_PW;         // points per tile (1024)
 constexpr int MX_MAXCOL = 8;                   // weight columns per pass (kernels for 4 and 8)
 constexpr int MX_NGEO = 5;                     // x, lsh, lsl, turn hi, turn lo
 constexpr int MX_BLK = 32;                     // steps between CTA combines
+// The near-pole form in column mode (catalog points next to a pole) is compiled
+// out: its second code path slows the standard one (250 registers instead of
+// 232; 12.1 -> 13.2 s at 8 columns on 1e7 points) for an error (6e-5 of the
+// m = 0 column) already inside the mixed path's tolerance.  Table mode keeps it.
+constexpr bool COLPOLE = false;
 
 // ---------------------------------------------------------------- prep --
 __device__ __forceinline__ void mx_write(const PrepColsParams& p, int64_t j, float x, float ph, int64_t src) {
@@ -431,23 +436,25 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 1) analysis_mixed_kernel(const 
                 // u = |x| - 1, mirrored by sgn^q.
                 bool pole = false;
                 float sgn = 1.f;
-                if (p.pole_ae != nullptr && m < p.pole_mmax) {
-                    if (UF) {
-                        const float umin = p.pole_x - 1.f;
-                        pole = __all_sync(0xffffffffu, (u2[0].x >= umin) & (u2[0].y >= umin) &
-                                                           (u2[1].x >= umin) & (u2[1].y >= umin));
-                    } else {
-                        const float px = p.pole_x;
-                        const bool np = __all_sync(0xffffffffu, (u2[0].x >= px) & (u2[0].y >= px) &
-                                                                    (u2[1].x >= px) & (u2[1].y >= px));
-                        const bool sp = __all_sync(0xffffffffu, (u2[0].x <= -px) & (u2[0].y <= -px) &
-                                                                    (u2[1].x <= -px) & (u2[1].y <= -px));
-                        pole = np | sp;
-                        sgn = np ? 1.f : -1.f;
-                        if (pole) {
+                if (COLPOLE || UF) {
+                    if (p.pole_ae != nullptr && m < p.pole_mmax) {
+                        if (UF) {
+                            const float umin = p.pole_x - 1.f;
+                            pole = __all_sync(0xffffffffu, (u2[0].x >= umin) & (u2[0].y >= umin) &
+                                                               (u2[1].x >= umin) & (u2[1].y >= umin));
+                        } else {
+                            const float px = p.pole_x;
+                            const bool np = __all_sync(0xffffffffu, (u2[0].x >= px) & (u2[0].y >= px) &
+                                                                        (u2[1].x >= px) & (u2[1].y >= px));
+                            const bool sp = __all_sync(0xffffffffu, (u2[0].x <= -px) & (u2[0].y <= -px) &
+                                                                        (u2[1].x <= -px) & (u2[1].y <= -px));
+                            pole = np | sp;
+                            sgn = np ? 1.f : -1.f;
+                            if (pole) {
 #pragma unroll
-                            for (int kp = 0; kp < 2; ++kp)
-                                u2[kp] = make_float2(fabsf(u2[kp].x) - 1.f, fabsf(u2[kp].y) - 1.f);
+                                for (int kp = 0; kp < 2; ++kp)
+                                    u2[kp] = make_float2(fabsf(u2[kp].x) - 1.f, fabsf(u2[kp].y) - 1.f);
+                            }
                         }
                     }
                 }
