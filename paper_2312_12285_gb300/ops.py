@@ -222,7 +222,7 @@ def ntheta_for_tolerance(lmax: int, cl_tol: float = 1e-4, safety: float = 4.0) -
     err(N) <= cl_tol / safety (10 lmax for the default 1e-4 / 4), at most
     32768."""
     ratio = (cl_tol / safety / 4.3e-6) ** 0.25
-    n = int(math.ceil(16.0 * lmax / max(ratio, 1.0)))
+    n = int(math.ceil(16.0 * lmax / ratio))
     n += n & 1
     return max(2, min(32768, n))
 
