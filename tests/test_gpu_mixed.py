@@ -82,6 +82,23 @@ def small(dev, request):
     return L, x, phi, W, got, ref, kernel
 
 
+@pytest.mark.parametrize("shape", ["tcgen05:4x64", "tcgen05:2x128"])
+def test_tcgen05_other_shapes(dev, shape):
+    """The tcgen05 kernel's other producer / stage shapes (4 warps x 64
+    multipoles, 2 x 128) on 6 000 points (several tiles of their 256 and 128
+    points and a ragged last one) at lmax 200 with five columns, against the
+    oracle."""
+    L = 200
+    wl = catalogs.lognormal_cap(600, 5_400, L, config_id=33, nwaves=64, grid=(128, 256))
+    x, phi, W = catalogs.weight_columns(wl, 5)
+    got = _columns(dev, x, phi, W, L, kernel=shape)
+    x64, p64 = x.astype(np.float64), phi.astype(np.float64)
+    for f in range(5):
+        ref = oracle.alm(x64, p64, W[f].astype(np.float64), L)
+        assert oracle.rel_err_per_l(got[f], ref, L) <= TOL_CL, f
+        assert _cl_err(got[f], ref, L) <= TOL_CL, f
+
+
 def test_mixed_matches_oracle(small):
     L, _, _, _, got, ref, _ = small
     for f in NONZERO:
