@@ -201,6 +201,10 @@ size_t pointsht_workspace_size(pointsht_plan plan, const pointsht_catalog* cats,
  * 256-byte aligned, contents need not be initialised and are clobbered.
  * Every step (point preparation, the per-point recurrences, the sums over
  * points and the final reduction) runs in this library's kernels.
+ * lmax limits: FP32 4096 (the recurrence's exponent handling); FP64 the
+ * largest lmax whose per-warp accumulator rows fit in the device's shared
+ * memory (2970 on a GB300).  A larger plan is refused with EINVAL, whose
+ * message names the bound.
  * Errors: EINVAL on bad arguments, ENOMEM if ws_bytes is too small. */
 pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catalog* cats, int32_t ncat,
                              int32_t nfield, pointsht_precision prec, double* alm_out,

@@ -1517,6 +1517,18 @@ int analysis_tile_points(int prec_is_f64, int k32) {
     return 32 * k32;
 }
 
+// shared memory one CTA of the analysis launch needs at this lmax (the per-warp
+// accumulator rows grow with lmax)
+size_t analysis_smem_need(int prec_is_f64, int k32, int lmax) {
+    if (prec_is_f64) return analysis_smem_bytes<TraitsF64, 4, 4>(lmax);
+    switch (k32) {
+        case 8: return analysis_smem_bytes<TraitsF32, 8, 4>(lmax);
+        case 12: return analysis_smem_bytes<TraitsF32, 12, 4>(lmax);
+        case 108: return analysis_f32g_smem_bytes<8, 4, 4>(lmax);
+        default: return analysis_smem_bytes<TraitsF32, 16, 4>(lmax);
+    }
+}
+
 cudaError_t launch_analysis(const AnalysisParams& ap, int prec_is_f64, int k32, int sm_count, cudaStream_t st,
                             int* grid) {
     if (prec_is_f64) return launch_analysis_t<TraitsF64, 4, 4>(ap, sm_count, st, grid);

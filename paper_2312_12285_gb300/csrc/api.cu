@@ -36,6 +36,7 @@ cudaError_t launch_build_gtab(int, int, int, const double*, const double*, const
 int adjoint_points_per_warp(int);
 cudaError_t launch_adjoint(int, const AdjointParams&, cudaStream_t);
 int adjoint_sorted_points_per_cta();
+size_t analysis_smem_need(int prec_is_f64, int k32, int lmax);
 size_t coupling_smem_bytes(int);
 size_t spin2_workspace_bytes(int, const pointsht_shear_catalog*, int, int);
 cudaError_t spin2_run(int, const pointsht_shear_catalog*, int, int, void*, unsigned*, int, double*, double*,
@@ -71,6 +72,7 @@ struct pointsht_plan_s {
     int lmax = 0;
     int device = 0;
     int sm_count = 0;
+    size_t smem_optin = 0;       // the device's opt-in shared memory per block
     int64_t nmodes = 0;
     int64_t acol = 0;  // colstart[lmax+1]: padded column-table length
     void* blob = nullptr;
@@ -253,6 +255,11 @@ extern "C" pointsht_status pointsht_plan_create(int32_t lmax, pointsht_plan* out
     p->lmax = lmax;
     p->device = dev;
     p->sm_count = sms;
+    {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        p->smem_optin = (size_t)v;
+    }
     p->nmodes = (int64_t)(lmax + 1) * (lmax + 2) / 2;
     p->acol = colstart[lmax + 1];
     if (cudaMalloc(&p->blob, total) != cudaSuccess) {
@@ -571,6 +578,13 @@ extern "C" pointsht_status pointsht_alm(pointsht_plan plan, const pointsht_catal
     if ((s = check_device(plan, "alm")) != POINTSHT_OK) return s;
     Layout lo;
     make_layout(plan, cats, ncat, nfield, prec, lo);
+    if (plan->smem_optin && analysis_smem_need(lo.is_f64, lo.k32, plan->lmax) > plan->smem_optin) {
+        // the per-warp accumulator rows of the analysis CTA live in shared memory
+        int lm = 1;
+        while (lm < plan->lmax && analysis_smem_need(lo.is_f64, lo.k32, lm + 1) <= plan->smem_optin) ++lm;
+        return fail(POINTSHT_EINVAL, "alm: the %s path supports lmax <= %d on this device (plan has %d)",
+                    lo.is_f64 ? "FP64" : "FP32", lm, plan->lmax);
+    }
     if ((s = check_ws(lo, workspace, ws_bytes, lo.total, "alm")) != POINTSHT_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(workspace);

@@ -1,0 +1,135 @@
+"""Extremes of the multipole range: the smallest lmax (1, 2, 3: columns of one
+or two steps, order pairs that are a single column) through every path, and
+the largest lmax each path supports (FP32 recurrence 4096; FP64 the largest
+whose accumulator rows fit in shared memory, 2970 on a GB300) on single points
+and a small catalog, against the FP64 oracle.
+
+Tolerances: FP64 path 1e-10 relative per multipole row (1e-13 on single-point
+identities); FP32 path 1e-5 relative per row at low lmax, and at lmax 4096 the
+single-point addition theorem C_l = w^2/4pi within 4e-5 (the FP32 recurrence
+carries ~l eps per value); mixed path and interpolated route 1e-4 / 1e-5 as in
+their own test files.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2312_12285_gb300 import catalogs, ops  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+FOUR_PI = 4.0 * np.pi
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)
+
+
+def _points(n, seed, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    x, phi = catalogs.uniform_sphere(rng, n, dtype)
+    w = rng.uniform(0.5, 1.5, n).astype(dtype)
+    return x, phi, w
+
+
+def _cat(dev, x, phi, w, field=0, coeff=1.0):
+    return ops.Cat(*(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (x, phi, w)), field, coeff)
+
+
+def _alm(dev, cats, L, prec, nfield=1):
+    plan = ops.get_plan(L, dev)
+    a = ops.alm_raw(plan, cats, nfield, prec)
+    torch.cuda.synchronize()
+    plan.check()
+    return a.cpu().numpy()
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_lmax_transform_and_adjoint(dev, L, prec):
+    dt = np.float64 if prec == "fp64" else np.float32
+    x, phi, w = _points(3001, 700 + L, dt)
+    ref = oracle.alm(x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64) * -0.7, L)
+    got = _alm(dev, [_cat(dev, x, phi, w, 0, -0.7)], L, prec)[0]
+    assert got.shape == ref.shape == (oracle.nmodes(L),)
+    assert oracle.rel_err_per_l(got, ref, L) <= (1e-10 if prec == "fp64" else 1e-5)
+    # adjoint with a random cotangent
+    rng = np.random.default_rng(L)
+    M = oracle.nmodes(L)
+    g = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    plan = ops.get_plan(L, dev)
+    (gw,) = ops.alm_backward_raw(plan, [_cat(dev, x, phi, w, 0, -0.7)], 1, prec, torch.from_numpy(g).to(dev))
+    torch.cuda.synchronize()
+    plan.check()
+    r = -0.7 * oracle.adjoint(x.astype(np.float64), phi.astype(np.float64), g[0], L)
+    got_g = gw.double().cpu().numpy()
+    assert np.max(np.abs(got_g - r)) <= (1e-11 if prec == "fp64" else 2e-5) * np.max(np.abs(r))
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_tiny_lmax_mixed_and_interpolated(dev, L):
+    x, phi, w = _points(2500, 800 + L)
+    rng = np.random.default_rng(900 + L)
+    W = np.stack([w, rng.uniform(0.8, 1.2, x.size).astype(np.float32), rng.standard_normal(x.size).astype(np.float32)])
+    plan = ops.get_plan(L, dev)
+    x64, p64 = x.astype(np.float64), phi.astype(np.float64)
+    for kernel in ("mma.sync", "tcgen05"):
+        plan.set_mixed_kernel(kernel)
+        try:
+            got = ops.alm_columns(plan, torch.from_numpy(x).to(dev), torch.from_numpy(phi).to(dev),
+                                  torch.from_numpy(np.ascontiguousarray(W)).to(dev), "mixed").cpu().numpy()
+            plan.check()
+        finally:
+            plan.set_mixed_kernel("mma.sync")
+        for f in range(3):
+            ref = oracle.alm(x64, p64, W[f].astype(np.float64), L)
+            assert oracle.rel_err_per_l(got[f], ref, L) <= 1e-4, (kernel, f)
+    nt = 16 * L
+    gi = ops.alm_interp(plan, [_cat(dev, x, phi, w)], 1, nt).cpu().numpy()[0]
+    plan.check()
+    ri = oracle.alm_interp(x64, p64, w.astype(np.float64), L, nt)
+    assert oracle.rel_err_per_l(gi, ri, L) <= 1e-5
+
+
+def test_fp32_max_lmax_single_points_and_catalog(dev):
+    """lmax 4096, the FP32 recurrence's limit: single points at x = 0.31, 0,
+    0.97 and 1 obey the addition theorem C_l = w^2/4pi at every l, and 200
+    random points match the oracle row by row."""
+    L = 4096
+    for xv in (0.31, 0.0, 0.97, 1.0):
+        c = _cat(dev, np.array([xv], np.float32), np.array([1.3], np.float32), np.array([1.7], np.float32))
+        a = _alm(dev, [c], L, "fp32")[0]
+        cl = oracle.cl(a, a, L)
+        assert np.max(np.abs(cl / (1.7 ** 2 / FOUR_PI) - 1.0)) <= 4e-5, xv
+    x, phi, w = _points(200, 4096)
+    got = _alm(dev, [_cat(dev, x, phi, w)], L, "fp32")[0]
+    ref = oracle.alm(x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64), L)
+    assert oracle.rel_err_per_l(got, ref, L) <= 1e-4
+
+
+def test_fp64_max_lmax(dev):
+    """The FP64 analysis keeps a CTA's per-warp accumulator rows in shared
+    memory, so its lmax is bounded by the device (2970 on a GB300, below the
+    plan's 8192): a larger plan is refused with EINVAL naming the bound, and at
+    the bound a single point at x = -0.42 obeys the addition theorem to 1e-12
+    and 60 random points match the oracle row by row to 1e-10."""
+    import re
+    from paper_2312_12285_gb300 import _lib
+    c = _cat(dev, np.array([-0.42]), np.array([0.4]), np.array([0.9]))
+    with pytest.raises(_lib.PointSHTError) as err:
+        _alm(dev, [c], 8192, "fp64")
+    assert err.value.status == _lib.EINVAL
+    L = int(re.search(r"lmax <= (\d+)", str(err.value)).group(1))
+    assert 2048 <= L < 8192
+    a = _alm(dev, [c], L, "fp64")[0]
+    cl = oracle.cl(a, a, L)
+    assert np.max(np.abs(cl / (0.9 ** 2 / FOUR_PI) - 1.0)) <= 1e-12
+    x, phi, w = _points(60, 8192, np.float64)
+    got = _alm(dev, [_cat(dev, x, phi, w)], L, "fp64")[0]
+    ref = oracle.alm(x, phi, w, L)
+    assert oracle.rel_err_per_l(got, ref, L) <= 1e-10
