@@ -112,6 +112,28 @@ def test_fp32_max_lmax_single_points_and_catalog(dev):
     assert oracle.rel_err_per_l(got, ref, L) <= 1e-4
 
 
+def test_weight_columns_at_fp32_max_lmax(dev):
+    """Weight columns at lmax 4096 through both contraction kernels (the
+    tcgen05 kernel's coefficient copies grow with lmax: ~207 KB of shared
+    memory there): 1 500 points, two columns, against the oracle."""
+    L = 4096
+    x, phi, w = _points(1500, 4097)
+    W = np.stack([w, np.random.default_rng(4098).standard_normal(x.size).astype(np.float32)])
+    plan = ops.get_plan(L, dev)
+    x64, p64 = x.astype(np.float64), phi.astype(np.float64)
+    ref = [oracle.alm(x64, p64, W[f].astype(np.float64), L) for f in range(2)]
+    for kernel in ("mma.sync", "tcgen05"):
+        plan.set_mixed_kernel(kernel)
+        try:
+            got = ops.alm_columns(plan, torch.from_numpy(x).to(dev), torch.from_numpy(phi).to(dev),
+                                  torch.from_numpy(np.ascontiguousarray(W)).to(dev), "mixed").cpu().numpy()
+            plan.check()
+        finally:
+            plan.set_mixed_kernel("mma.sync")
+        for f in range(2):
+            assert oracle.rel_err_per_l(got[f], ref[f], L) <= 1e-4, (kernel, f)
+
+
 def test_fp64_max_lmax(dev):
     """The FP64 analysis keeps a CTA's per-warp accumulator rows in shared
     memory, so its lmax is bounded by the device (2970 on a GB300, below the
