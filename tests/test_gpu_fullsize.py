@@ -1,9 +1,11 @@
-"""Parity at the benchmark's full size and launch configuration: 1e6 lognormal
-galaxies + 9e6 randoms in the cap mask, lmax 2048, FP32 path, through the C
-ABI exactly as bench.py calls it.  The oracle cannot finish the whole
-triangle in seconds, so it computes whole m-columns over all 1e7 points:
-m = 0 (largest values, strongest data - alpha * randoms cancellation at low
-l), and the short columns m = 1900, 2047, 2048 (deepest below-range seeds).
+"""Parity at full size and in the launch configuration bench.py times, FP32
+path through the C ABI, on the two plain-FP32 workloads: 1e6 lognormal
+galaxies + 9e6 randoms in the cap mask at lmax 2048 (the benchmark's), and
+1e6 galaxies + 1e7 randoms in the same mask at lmax 1024.  The oracle cannot
+finish the whole triangle in seconds, so it computes whole m-columns over all
+points: m = 0 (largest values, strongest data - alpha * randoms cancellation
+at low l), and three short columns up to m = lmax (deepest below-range
+seeds).
 
 Tolerance: relative L2 error of each column <= 1e-5 (FP32 recurrence with
 FP64-accurate seeds and phases), except m = 0 (see below)."""
@@ -18,32 +20,37 @@ from paper_2312_12285_gb300 import catalogs, ops  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def run():
+# workload -> (point count, oracle columns)
+WORKLOADS = {2: (11_000_000, (0, 900, 1023, 1024)), 3: (10_000_000, (0, 1900, 2047, 2048))}
+
+
+@pytest.fixture(scope="module", params=sorted(WORKLOADS), ids=["lognormal_cap_l1024", "lognormal_cap_l2048"])
+def run(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     dev = torch.device("cuda", 0)
-    wl = catalogs.config(3)
+    wl = catalogs.config(request.param)
     cats = [ops.Cat(torch.from_numpy(c.x).to(dev), torch.from_numpy(c.phi).to(dev), torch.from_numpy(c.w).to(dev),
                     c.field, c.coeff) for c in wl.catalogs]
     plan = ops.get_plan(wl.lmax, dev)
     a = ops.alm_raw(plan, cats, 1, "fp32")
     torch.cuda.synchronize()
     plan.check()
-    return wl, a.cpu().numpy()[0]
+    return wl, a.cpu().numpy()[0], WORKLOADS[request.param]
 
 
 def test_fullsize_sampled_columns(run):
-    wl, a = run
+    wl, a, (npts, cols) = run
     L = wl.lmax
     x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
     phi = np.concatenate([c.phi.astype(np.float64) for c in wl.catalogs])
     w = np.concatenate([c.w.astype(np.float64) * c.coeff for c in wl.catalogs])
-    assert x.shape[0] == 10_000_000
+    assert x.shape[0] == npts
+    assert cols[-1] == L
     # m = 0 carries the points near the pole, where the plain FP32 recurrence's
     # error grows to ~1e-3 of lambda_max by l ~ 2048 (double root at x = 1);
     # tiles of points with |x| >= 0.9 run the near-pole form instead.
-    tol = {0: 1e-5, 1900: 1e-5, 2047: 1e-5, 2048: 1e-5}
+    tol = {m: 1e-5 for m in cols}
     ref = oracle.alm(x, phi, w, L, mlist=list(tol))
     for m in tol:
         col = a[oracle.index(m, m, L):oracle.index(L, m, L) + 1]
@@ -54,7 +61,7 @@ def test_fullsize_sampled_columns(run):
 def test_fullsize_monopole_and_dipole_exact_sums(run):
     """a_00 = sum_i s_i w_i / sqrt(4 pi) and a_10 = sqrt(3/4pi) sum_i s_i w_i x_i
     hold at any size (closed forms of Y_00 and Y_10)."""
-    wl, a = run
+    wl, a, _ = run
     x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
     w = np.concatenate([c.w.astype(np.float64) * c.coeff for c in wl.catalogs])
     a00 = np.sum(w) / np.sqrt(4 * np.pi)
@@ -67,8 +74,8 @@ def test_fullsize_monopole_and_dipole_exact_sums(run):
 def test_fullsize_low_l_pseudo_cl(run):
     """Full-size C_l for 1 <= l <= 32, where the window is largest and the
     data - alpha * randoms cancellation strongest: the oracle transforms all
-    1e7 points to lmax 32 (a_lm for l <= 32 does not depend on lmax)."""
-    wl, a = run
+    points to lmax 32 (a_lm for l <= 32 does not depend on lmax)."""
+    wl, a, _ = run
     L = wl.lmax
     Ls = 32
     x = np.concatenate([c.x.astype(np.float64) for c in wl.catalogs])
