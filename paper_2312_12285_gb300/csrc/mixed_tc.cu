@@ -245,7 +245,9 @@ __global__ void __launch_bounds__(TcShape<PW, NB>::THREADS, 1)
 
     uint32_t gb = 0;            // blocks of this CTA so far (stage gb & 1, phase (gb >> 1) & 1)
     uint32_t tile_parity = 0;
-    bool tile_pending = false;  // a tile copy is in flight (thread 32, the first producer)
+    bool tile_pending = false;  // a tile copy is owed to tile_bar (thread 32, which issues the copies)
+    bool coef_owed = false;     // thread 32 gave up on a coefficient copy: owed to coef_bar
+    uint32_t coef_owed_parity = 0;
 
     for (;;) {
         if (threadIdx.x == 0) sh->unit = (int64_t)atomicAdd(p.counter, 1);
@@ -291,6 +293,10 @@ __global__ void __launch_bounds__(TcShape<PW, NB>::THREADS, 1)
         if (prod && !mbar_wait_bounded(&sh->coef_bar, coef_parity)) {
             atomicOr(p.err, ERR_TIMEOUT);
             sh->abort = 1;
+            if (threadIdx.x == 32) {  // the copy may still land: drained before the CTA leaves
+                coef_owed = true;
+                coef_owed_parity = coef_parity;
+            }
         }
         coef_parity ^= 1u;
 
@@ -301,9 +307,11 @@ __global__ void __launch_bounds__(TcShape<PW, NB>::THREADS, 1)
                     atomicOr(p.err, ERR_TIMEOUT);
                     sh->abort = 1;
                 }
+                // a copy thread 32 gave up on stays owed, on this phase, until
+                // the drain below (no further tile is issued once aborted)
+                if (threadIdx.x == 32 && ok) tile_pending = false;
             }
-            tile_parity ^= 1u;
-            if (threadIdx.x == 32) tile_pending = false;
+            if (!tile_pending) tile_parity ^= 1u;
             const float* tf = reinterpret_cast<const float*>(tile);
             const uint32_t* tu = reinterpret_cast<const uint32_t*>(tile);
 
@@ -586,6 +594,7 @@ __global__ void __launch_bounds__(TcShape<PW, NB>::THREADS, 1)
     if (prod) named_sync(2, S::PT);  // the control warp's last "W read" arrival
     __syncthreads();
     if (threadIdx.x == 32 && tile_pending) mbar_drain(&sh->tile_bar, tile_parity);
+    if (threadIdx.x == 32 && coef_owed) mbar_drain(&sh->coef_bar, coef_owed_parity);
     if (ctl) {
         // the last issued block's MMAs: its empty phase (if any block was issued)
         if (gb > 0) {
