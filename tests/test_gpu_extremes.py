@@ -155,3 +155,44 @@ def test_fp64_max_lmax(dev):
     got = _alm(dev, [_cat(dev, x, phi, w)], L, "fp64")[0]
     ref = oracle.alm(x, phi, w, L)
     assert oracle.rel_err_per_l(got, ref, L) <= 1e-10
+
+
+def test_more_than_2_31_points_in_one_field(dev):
+    """One field of 2 147 975 181 points (> 2^31; a 65 549-point seeded
+    pattern repeated 32 769 times on the device, so the field also ends in a
+    ragged, padded tail), lmax 64, FP32 path and its adjoint: every point
+    index, sort range, chunk and point id past 2^31 is in use.  Expected
+    values from the oracle on the pattern alone: a_lm = R x the pattern's a_lm
+    (1e-4 per multipole row, the FP32 path's bound; a_00 to 1e-5), and the
+    gradient of every copy equals the oracle gradient of its pattern point
+    (2e-5 of the largest, as at small sizes), checked on 200 000 random copies
+    and on the copies around index 2^31 and at the end."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 110e9:
+        pytest.skip("needs ~100 GB of free device memory")
+    L, npat, R = 64, 65_549, 32_769
+    n = npat * R
+    assert n > 2**31
+    x, phi, w = _points(npat, 2**31)
+    xt, pt, wt = (torch.from_numpy(v).to(dev).repeat(R) for v in (x, phi, w))
+    cat = ops.Cat(xt, pt, wt, 0, 1.0)
+    x64, p64, w64 = x.astype(np.float64), phi.astype(np.float64), w.astype(np.float64)
+    a = _alm(dev, [cat], L, "fp32")[0]
+    ref = R * oracle.alm(x64, p64, w64, L)
+    assert oracle.rel_err_per_l(a, ref, L) <= 1e-4
+    a00 = R * np.sum(w64) / np.sqrt(FOUR_PI)
+    assert abs(a[0] - a00) <= 1e-5 * a00
+    rng = np.random.default_rng(2**31 + 1)
+    M = oracle.nmodes(L)
+    g = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    plan = ops.get_plan(L, dev)
+    (gw,) = ops.alm_backward_raw(plan, [cat], 1, "fp32", torch.from_numpy(g).to(dev))
+    torch.cuda.synchronize()
+    plan.check()
+    idx = np.concatenate([rng.integers(0, n, 200_000), np.arange(2**31 - 1000, 2**31 + 1000),
+                          np.arange(n - 1000, n)]).astype(np.int64)
+    got = gw[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+    r = oracle.adjoint(x64, p64, g[0], L)[idx % npat]
+    assert np.max(np.abs(got - r)) <= 2e-5 * np.max(np.abs(r))
+    del xt, pt, wt, cat, gw
+    torch.cuda.empty_cache()
