@@ -196,3 +196,33 @@ def test_more_than_2_31_points_in_one_field(dev):
     assert np.max(np.abs(got - r)) <= 2e-5 * np.max(np.abs(r))
     del xt, pt, wt, cat, gw
     torch.cuda.empty_cache()
+
+
+def test_weight_columns_more_than_2_31_points(dev):
+    """Two weight columns on 2 147 975 181 points (the 65 549-point pattern
+    repeated 32 769 times), lmax 64, through both contraction kernels:
+    alm = R x the oracle's a_lm of the pattern, column by column, at the
+    mixed path's 1e-4 per multipole row."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 110e9:
+        pytest.skip("needs ~100 GB of free device memory")
+    L, npat, R = 64, 65_549, 32_769
+    x, phi, w = _points(npat, 2**31)
+    w2 = np.random.default_rng(2**31 + 2).standard_normal(npat).astype(np.float32)
+    xt, pt = (torch.from_numpy(v).to(dev).repeat(R) for v in (x, phi))
+    W = torch.from_numpy(np.stack([w, w2])).to(dev).repeat(1, R)
+    assert W.is_contiguous() and W.shape == (2, npat * R)
+    x64, p64 = x.astype(np.float64), phi.astype(np.float64)
+    ref = [R * oracle.alm(x64, p64, c.astype(np.float64), L) for c in (w, w2)]
+    plan = ops.get_plan(L, dev)
+    for kernel in ("mma.sync", "tcgen05"):
+        plan.set_mixed_kernel(kernel)
+        try:
+            got = ops.alm_columns(plan, xt, pt, W, "mixed").cpu().numpy()
+            plan.check()
+        finally:
+            plan.set_mixed_kernel("mma.sync")
+        for f in range(2):
+            assert oracle.rel_err_per_l(got[f], ref[f], L) <= 1e-4, (kernel, f)
+    del xt, pt, W
+    torch.cuda.empty_cache()
