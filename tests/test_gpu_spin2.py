@@ -170,3 +170,23 @@ def test_fullsize_low_l_spectra(fullsize):
         sub = np.concatenate([got[oracle.index(m, m, L):oracle.index(Ls, m, L) + 1] for m in range(Ls + 1)])
         c, r = oracle.cl(sub, sub, Ls), oracle.cl(ref, ref, Ls)
         assert np.max(np.abs(c[2:] - r[2:]) / r[2:]) <= 1e-5
+
+
+def test_more_than_2_31_points(dev):
+    """One field of 2 147 975 181 shear points (> 2^31; a 65 549-point
+    seeded pattern repeated 32 769 times on the device, ragged tail), lmax 64:
+    every point index, sort range and chunk offset past 2^31 in use.  E_lm and
+    B_lm = R x the oracle's on the pattern, at 1e-4 per multipole row (the
+    scalar FP32 path's bound at this size: the pattern's sums cancel ~256-fold)."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 135e9:
+        pytest.skip("needs ~125 GB of free device memory")
+    L, npat, R = 64, 65_549, 32_769
+    arrs = _shear(npat, 2**31)
+    cat = ops.ShearCat(*(torch.from_numpy(a).to(dev).repeat(R) for a in arrs), 0, 1.0)
+    E, B = _run(dev, L, [cat])
+    Er, Br = _ref(arrs, L)
+    for got, ref in ((E[0], R * Er), (B[0], R * Br)):
+        assert _per_l_err(got, ref, L) <= 1e-4
+    del cat
+    torch.cuda.empty_cache()
