@@ -226,3 +226,35 @@ def test_weight_columns_more_than_2_31_points(dev):
             assert oracle.rel_err_per_l(got[f], ref[f], L) <= 1e-4, (kernel, f)
     del xt, pt, W
     torch.cuda.empty_cache()
+
+
+def test_fp64_more_than_2_31_points(dev):
+    """The FP64 path and its catalog-order adjoint on one field of
+    2 147 975 181 points (the 65 549-point pattern, in float64, repeated
+    32 769 times), lmax 16: a_lm = R x the oracle's a_lm of the pattern
+    (1e-10 per multipole row) and the gradient of every copy equals the
+    oracle's gradient of its pattern point (1e-11 of the largest), sampled
+    around index 2^31 and at the end."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 150e9:
+        pytest.skip("needs ~140 GB of free device memory")
+    L, npat, R = 16, 65_549, 32_769
+    n = npat * R
+    x, phi, w = _points(npat, 2**31 + 3, np.float64)
+    cat = ops.Cat(*(torch.from_numpy(v).to(dev).repeat(R) for v in (x, phi, w)), 0, 1.0)
+    a = _alm(dev, [cat], L, "fp64")[0]
+    assert oracle.rel_err_per_l(a, R * oracle.alm(x, phi, w, L), L) <= 1e-10
+    rng = np.random.default_rng(2**31 + 4)
+    M = oracle.nmodes(L)
+    g = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    plan = ops.get_plan(L, dev)
+    (gw,) = ops.alm_backward_raw(plan, [cat], 1, "fp64", torch.from_numpy(g).to(dev))
+    torch.cuda.synchronize()
+    plan.check()
+    idx = np.concatenate([rng.integers(0, n, 200_000), np.arange(2**31 - 1000, 2**31 + 1000),
+                          np.arange(n - 1000, n)]).astype(np.int64)
+    got = gw[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    r = oracle.adjoint(x, phi, g[0], L)[idx % npat]
+    assert np.max(np.abs(got - r)) <= 1e-11 * np.max(np.abs(r))
+    del cat, gw
+    torch.cuda.empty_cache()
