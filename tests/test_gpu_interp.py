@@ -170,6 +170,24 @@ def test_argument_errors(dev):
         assert ei.value.status == _lib.EINVAL
 
 
+def test_field_of_2_31_points_is_refused(dev):
+    """The route's binning counts are 32-bit, so a field of 2^31 points or
+    more is refused on the host before anything is enqueued: two catalogs of
+    2^30 points on one field give EINVAL naming the limit and a zero
+    workspace size, while 2^31 - 1 points pass the size query.  The call is
+    made with NULL output and workspace (and catalogs whose arrays are far
+    shorter than their counts), so no kernel could run even past the check."""
+    plan = ops.get_plan(8, dev)
+    t = torch.zeros(32, dtype=torch.float32, device=dev)
+    p = t.data_ptr()
+    arr, n = _lib.catalog_array([(p, p, p, 1 << 30, 0, 1.0)] * 2)
+    assert plan.lib.pointsht_workspace_size_interp(plan.handle, arr, n, 1, 64) == 0
+    assert plan.lib.pointsht_alm_interp(plan.handle, arr, n, 1, 64, None, None, 0, None) == _lib.EINVAL
+    assert "2^31 or more points" in _lib.last_error()
+    arr, n = _lib.catalog_array([(p, p, p, 1 << 30, 0, 1.0), (p, p, p, (1 << 30) - 1, 0, 1.0)])
+    assert plan.lib.pointsht_workspace_size_interp(plan.handle, arr, n, 1, 64) > 0
+
+
 # ------------------------------------------------------------------ full size --
 @pytest.fixture(scope="module")
 def full(dev):
