@@ -167,6 +167,7 @@ def test_more_than_2_31_points_in_one_field(dev):
     gradient of every copy equals the oracle gradient of its pattern point
     (2e-5 of the largest, as at small sizes), checked on 200 000 random copies
     and on the copies around index 2^31 and at the end."""
+    torch.cuda.empty_cache()  # blocks cached by earlier tests count as used
     free, _ = torch.cuda.mem_get_info()
     if free < 110e9:
         pytest.skip("needs ~100 GB of free device memory")
@@ -203,6 +204,7 @@ def test_weight_columns_more_than_2_31_points(dev):
     repeated 32 769 times), lmax 64, through both contraction kernels:
     alm = R x the oracle's a_lm of the pattern, column by column, at the
     mixed path's 1e-4 per multipole row."""
+    torch.cuda.empty_cache()  # blocks cached by earlier tests count as used
     free, _ = torch.cuda.mem_get_info()
     if free < 110e9:
         pytest.skip("needs ~100 GB of free device memory")
@@ -235,6 +237,7 @@ def test_fp64_more_than_2_31_points(dev):
     (1e-10 per multipole row) and the gradient of every copy equals the
     oracle's gradient of its pattern point (1e-11 of the largest), sampled
     around index 2^31 and at the end."""
+    torch.cuda.empty_cache()  # blocks cached by earlier tests count as used
     free, _ = torch.cuda.mem_get_info()
     if free < 150e9:
         pytest.skip("needs ~140 GB of free device memory")
