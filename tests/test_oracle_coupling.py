@@ -168,3 +168,32 @@ def test_binned_full_sky_and_piecewise_constant_recovery():
     Minv, Mcal, dec = oracle.decouple(Mbb, R, (oracle.bin_matrix(edges, L) @ (M @ C))[None])
     assert np.max(np.abs(Mcal @ C - Cb)) <= 1e-12 * np.max(Cb)
     assert np.max(np.abs(dec[0] - Cb)) <= 1e-12 * np.max(Cb)
+
+
+@pytest.mark.parametrize("L,lw", [(0, 0), (1, 5), (7, 3), (40, 80), (40, 100), (25, 10)])
+def test_coupling_row_matches_matrix(L, lw):
+    """oracle.coupling_row (one row, for the large-lmax GPU comparisons) is
+    row l of the pinned matrix: M_ll' carries (2l'+1), so it is not
+    symmetric and a transposed or shifted row fails."""
+    W = np.random.default_rng(L * 1000 + lw).uniform(0.1, 2.0, lw + 1)
+    M = oracle.coupling(W, L)
+    if L > 2:
+        assert not np.allclose(M, M.T)
+    for l in range(L + 1):
+        row = oracle.coupling_row(W, L, l)
+        assert np.max(np.abs(row - M[l])) <= 1e-13 * max(1.0, np.max(np.abs(M[l]))), l
+
+
+def test_window_cl_single_point_and_noise():
+    """W_l of one point of weight w is w^2/4pi at every l (addition theorem);
+    subtracting the shot-noise constant w^2/4pi (the footnote to Eq. wldef)
+    leaves zero, and two coincident points give 4 w^2/4pi against a noise
+    of 2 w^2/4pi."""
+    L, w = 60, 1.7
+    x, phi = np.array([0.37]), np.array([2.1])
+    a = oracle.alm(x, phi, np.array([w]), L)
+    n1 = w * w / FOUR_PI
+    assert np.max(np.abs(oracle.window_cl(a, L) - n1)) <= 1e-13 * n1
+    assert np.max(np.abs(oracle.window_cl(a, L, n1))) <= 1e-13 * n1
+    a2 = oracle.alm(np.repeat(x, 2), np.repeat(phi, 2), np.array([w, w]), L)
+    assert np.max(np.abs(oracle.window_cl(a2, L, 2 * n1) - 2 * n1)) <= 1e-13 * n1
