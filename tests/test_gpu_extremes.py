@@ -1,8 +1,11 @@
-"""Extremes of the multipole range: the smallest lmax (1, 2, 3: columns of one
-or two steps, order pairs that are a single column) through every path, and
-the largest lmax each path supports (FP32 recurrence 4096; FP64 the largest
-whose accumulator rows fit in shared memory, 2970 on a GB300) on single points
-and a small catalog, against the FP64 oracle.
+"""Extremes of size, against the FP64 oracle: the smallest lmax (1, 2, 3:
+columns of one or two steps, order pairs that are a single column) through
+every path; the largest lmax each path supports (FP32 recurrence 4096; FP64
+the largest whose accumulator rows fit in shared memory, 2970 on a GB300) on
+single points and small catalogs; and one field of more than 2^31 points (a
+seeded pattern repeated on the device, so that the oracle's values for the
+pattern give the expected ones) through the FP32 path and its adjoint, both
+weight-column kernels, and the FP64 path and its adjoint.
 
 Tolerances: FP64 path 1e-10 relative per multipole row (1e-13 on single-point
 identities); FP32 path 1e-5 relative per row at low lmax, and at lmax 4096 the
