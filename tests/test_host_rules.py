@@ -1,5 +1,11 @@
-"""Host-side rules of the binding (no GPU): the interpolated route's sample
-count chosen from a pseudo-C_l error budget."""
+"""Host-side rules (no GPU): the interpolated route's sample count chosen
+from a pseudo-C_l error budget, and bench.py's --gpus N outside torchrun
+refusing to run fewer ranks than asked for."""
+import json
+import os
+import subprocess
+import sys
+
 import pytest
 
 from paper_2312_12285_gb300 import ops
@@ -34,3 +40,19 @@ def test_ntheta_benchmark_value():
     # the sample count the bench's interpolated lines use at lmax 2048 and 1536
     assert ops.ntheta_for_tolerance(2048, 1e-4) == 21104
     assert ops.ntheta_for_tolerance(1536, 1e-4) == 15828
+
+
+def test_bench_gpus_refuses_missing_gpus():
+    """--gpus N > 1 without WORLD_SIZE starts N ranks itself; on a node with
+    fewer than N GPUs it prints one JSON error line and exits 2 instead of
+    running (and reporting) fewer ranks."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--steps", "1"],
+                       capture_output=True, text=True, env=env, timeout=300, cwd=root)
+    assert r.returncode == 2, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert "--gpus 2" in line["error"]
