@@ -1,6 +1,7 @@
 """Host-side rules (no GPU): the interpolated route's sample count chosen
-from a pseudo-C_l error budget, and bench.py's --gpus N outside torchrun
-refusing to run fewer ranks than asked for."""
+from a pseudo-C_l error budget; bench.py's --gpus N outside torchrun
+refusing to run fewer ranks than asked for; and the JSON line of bench.py's
+reference arm (the oracle on the host cores)."""
 import json
 import os
 import subprocess
@@ -56,3 +57,32 @@ def test_bench_gpus_refuses_missing_gpus():
     assert r.returncode == 2, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert "--gpus 2" in line["error"]
+
+
+def _bench(args, extra_env=None):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                          env=env, timeout=600, cwd=root)
+
+
+def test_bench_reference_arm_line():
+    """--impl reference (the FP64 oracle timed on the host cores, on a bounded
+    sample of the workload) prints one JSON line with the contract's keys: the
+    same metric, unit and direction as the library's line, a cpu_baseline of
+    kind "oracle" naming its cores and sample, and an e2e block with no
+    host-device bytes; a rank other than 0 prints nothing and exits 0."""
+    args = ["--impl", "reference", "--steps", "1", "--warmup", "1", "--scale", "0.01", "--lmax", "256"]
+    r = _bench(args)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["higher_is_better"] is True
+    assert line["unit"] == "points*modes/s" and line["value"] > 0 and line["steps"] == 1
+    assert line["config"]["lmax"] == 256 and "lognormal_cap" in line["config"]["workload"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    r1 = _bench(args, {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r1.returncode == 0 and r1.stdout.strip() == "", (r1.stdout[-500:], r1.stderr[-2000:])
