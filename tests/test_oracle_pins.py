@@ -172,6 +172,42 @@ def test_addition_theorem_single_point_to_lmax_2048(oracle_mod):
     assert np.max(np.abs(c - oracle_mod.shot_noise([w]))) < 1e-11 * w * w / FOUR_PI
 
 
+def test_cross_noise_of_fields_sharing_randoms(oracle_mod):
+    """Fields a = D_a - alpha_a R and b = D_b - alpha_b R with distinct data
+    points but one random catalog R (Sec. 2.1, cross-spectra of tracers
+    sharing randoms): the only coincident (i = j) pairs of the cross-spectrum
+    are R's, so its noise is alpha_a alpha_b sum w_R^2 / 4pi, the off-diagonal
+    entry of the noise matrix the GPU test compares with.  With R alone (no
+    data) the cross-spectrum is exactly that at every l (addition theorem);
+    a wrong sign, a missing alpha or a data term in the cross entry fails."""
+    L = 300
+    xr, pr, wr = np.array([0.21, 0.21]), np.array([1.1, 1.1]), np.array([0.8, 1.3])  # coincident randoms
+    al_a, al_b = 0.08, 0.14
+    ra = oracle_mod.alm(xr, pr, -al_a * wr, L)
+    rb = oracle_mod.alm(xr, pr, -al_b * wr, L)
+    cross = oracle_mod.cl(ra, rb, L)
+    n_ab = al_a * al_b * np.sum(wr) ** 2 / FOUR_PI  # two coincident points: (sum w)^2
+    assert np.max(np.abs(cross / n_ab - 1)) < 1e-12
+    # one random point: the noise-matrix entry alpha_a alpha_b w^2 / 4pi itself
+    r1a = oracle_mod.alm(xr[:1], pr[:1], -al_a * wr[:1], L)
+    r1b = oracle_mod.alm(xr[:1], pr[:1], -al_b * wr[:1], L)
+    assert np.max(np.abs(oracle_mod.cl(r1a, r1b, L) - al_a * al_b * wr[0] ** 2 / FOUR_PI)) < 1e-13
+    # distinct data points in each field add no flat term to the cross-spectrum:
+    # its mean over l matches the noise entry only through R (random data positions)
+    rng = np.random.default_rng(5)
+    n = 4000
+    xa, pa = rng.uniform(-1, 1, n), rng.uniform(0, 2 * np.pi, n)
+    xb, pb = rng.uniform(-1, 1, n), rng.uniform(0, 2 * np.pi, n)
+    xs, ps = rng.uniform(-1, 1, 3 * n), rng.uniform(0, 2 * np.pi, 3 * n)
+    ws = rng.uniform(0.8, 1.2, 3 * n)
+    fa = oracle_mod.field_alm([(xa, pa, np.ones(n), 1.0), (xs, ps, ws, -al_a)], 64)
+    fb = oracle_mod.field_alm([(xb, pb, np.ones(n), 1.0), (xs, ps, ws, -al_b)], 64)
+    mean_cross = np.mean(oracle_mod.cl(fa, fb, 64)[1:])
+    n_ab = al_a * al_b * np.sum(ws * ws) / FOUR_PI
+    n_aa = (n + al_a ** 2 * np.sum(ws * ws)) / FOUR_PI
+    assert abs(mean_cross - n_ab) < 0.1 * n_aa  # unclustered: cross power is the shared noise, up to scatter
+
+
 def test_coincident_points(oracle_mod):
     L, n, w = 200, 5, 0.9
     a = oracle_mod.alm(np.full(n, -0.3), np.full(n, 4.0), np.full(n, w), L)
