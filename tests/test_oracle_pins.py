@@ -289,3 +289,28 @@ def test_single_point_gradient_closed_form(oracle_mod):
     gb = np.array([0.7, -1.1])
     (g,) = oracle_mod.grad_binned_cl([([0.2], [1.0], [w], 1.0)], L, edges, gb, [np.array([0])])
     assert abs(g[0]) < 1e-12
+
+
+def test_gradient_euler_identity(oracle_mod):
+    """L = sum_b g_b C_b is homogeneous of degree 2 in the weights (a_lm is
+    linear in them, C_l and the shot noise quadratic), so the oracle gradient
+    over every object obeys sum_i w_i dL/dw_i = 2 L exactly: a whole-sum check
+    that a dropped factor 2, a wrong c_m = 2 weight for m > 0 or a wrong sign
+    of the noise term fails (the identity the full-size GPU gradient is also
+    held to)."""
+    L = 48
+    rng = np.random.default_rng(31)
+    xg, pg, wg = rng.uniform(-1, 1, 300), rng.uniform(0, 2 * math.pi, 300), rng.uniform(0.8, 1.2, 300)
+    xr, pr, wr = rng.uniform(-1, 1, 900), rng.uniform(0, 2 * math.pi, 900), rng.uniform(0.8, 1.2, 900)
+    alpha = 0.31
+    edges = np.array([1, 3, 7, 15, 31, 49])
+    gb = rng.standard_normal(5)
+    cats = [(xg, pg, wg, 1.0), (xr, pr, wr, -alpha)]
+    a = oracle_mod.field_alm(cats, L)
+    n = oracle_mod.shot_noise(np.concatenate([wg, -alpha * wr]))
+    cb = oracle_mod.binned(oracle_mod.cl(a, a, L) - n, edges, L)
+    loss = float(np.dot(gb, cb))
+    gg, gr = oracle_mod.grad_binned_cl(cats, L, edges, gb, [np.arange(300), np.arange(900)])
+    s = float(np.dot(wg, gg) + np.dot(wr, gr))
+    scale = float(np.dot(np.abs(gb), np.abs(oracle_mod.binned(oracle_mod.cl(a, a, L), edges, L))))
+    assert abs(s - 2.0 * loss) <= 1e-12 * scale
