@@ -264,3 +264,39 @@ def test_fp64_more_than_2_31_points(dev):
     assert np.max(np.abs(got - r)) <= 1e-11 * np.max(np.abs(r))
     del cat, gw
     torch.cuda.empty_cache()
+
+
+def test_adjoint_and_spin2_at_fp32_max_lmax(dev):
+    """lmax 4096 through the FP32 adjoint (1 500 points, random cotangent)
+    and the spin-2 transform (800 points) against the oracle.  The FP32
+    recurrence carries ~l eps per value, so the bounds are those of lmax
+    4096: 3e-4 of the largest gradient, 1e-4 per multipole row of E and B."""
+    L = 4096
+    x, phi, w = _points(1500, 4099)
+    rng = np.random.default_rng(4100)
+    M = oracle.nmodes(L)
+    g = rng.standard_normal((1, M)) + 1j * rng.standard_normal((1, M))
+    plan = ops.get_plan(L, dev)
+    (gw,) = ops.alm_backward_raw(plan, [_cat(dev, x, phi, w)], 1, "fp32", torch.from_numpy(g).to(dev))
+    torch.cuda.synchronize()
+    plan.check()
+    r = oracle.adjoint(x.astype(np.float64), phi.astype(np.float64), g[0], L)
+    err = np.max(np.abs(gw.double().cpu().numpy() - r)) / np.max(np.abs(r))
+    print(f"adjoint lmax {L}: {err:.2e}")
+    assert err <= 3e-4
+    n = 800
+    xs, ps = rng.uniform(-1, 1, n), rng.uniform(0, 2 * np.pi, n)
+    ws, g1, g2 = rng.uniform(0.5, 1.5, n), 0.3 * rng.standard_normal(n), 0.3 * rng.standard_normal(n)
+    arrs = [v.astype(np.float32) for v in (xs, ps, ws, g1, g2)]
+    cat = ops.ShearCat(*(torch.from_numpy(a).to(dev) for a in arrs), 0, 1.0)
+    E, B = ops.alm_spin2(plan, [cat], 1)
+    torch.cuda.synchronize()
+    plan.check()
+    Er, Br = oracle.alm_spin2(*(a.astype(np.float64) for a in arrs), L)
+    lidx = np.concatenate([np.arange(m, L + 1) for m in range(L + 1)])  # l of each packed mode
+    for name, got, ref in (("E", E.cpu().numpy()[0], Er), ("B", B.cpu().numpy()[0], Br)):
+        num = np.bincount(lidx, np.abs(got - ref) ** 2, L + 1)
+        den = np.bincount(lidx, np.abs(ref) ** 2, L + 1)
+        worst = float(np.sqrt(np.max(num[2:] / den[2:])))
+        print(f"spin-2 {name} lmax {L}: {worst:.2e}")
+        assert worst <= 1e-4
