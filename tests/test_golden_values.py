@@ -19,13 +19,25 @@ them:
 """
 import json
 import os
+import shutil
 
 import numpy as np
+import pytest
 
 import oracle
 from paper_2312_12285_gb300 import catalogs
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(autouse=True)
+def _private_catalog_cache(tmp_path, monkeypatch):
+    """The two workloads are ~0.8 GB of drawn catalogs: cache them in this
+    test's temporary directory, outside the source tree, and drop them after."""
+    d = tmp_path / "catalogs"
+    monkeypatch.setenv("POINTSHT_CACHE_DIR", str(d))
+    yield
+    shutil.rmtree(d, ignore_errors=True)
 
 
 def test_tomographic_values_closed_forms_and_consistency():
